@@ -1,0 +1,330 @@
+"""Benchmark of the NPM hot path on GB300.
+
+Default workload (N=1): the paper-shaped FP32 model -- hash grid of 16 levels
+x 2 features (T = 2^19, resolutions 16..512), MLP 32-64-64-64-32, K = 8 --
+on 2^20 queries per step. One step = one npm_query_sample call over the batch
+(encode + decode + sample + pdf, one kernel). Inputs rotate over 8 batches
+(>= 300 MB, larger than L2) so every step reads cold inputs.
+
+Prints ONE JSON line (rank 0). Under torchrun each rank runs its own batch
+(weak scaling, no collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+HBM_FALLBACK_GBS = 6800.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": HBM_FALLBACK_GBS, "bf16_tflops": 1900.0,
+                "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_of(name):
+    return synth.WORKLOADS[name]
+
+
+def mlp_flops(w):
+    return 2 * sum(a * b for a, b in zip(w.widths[:-1], w.widths[1:]))
+
+
+def run_reference(args, w, rank):
+    """The oracle (FP64 CPU) timed on the host cores, a bounded sample per
+    step, on the same workload and metric."""
+    import oracle
+    oracle.build()
+    n = args.ref_sample
+    params = synth.random_params(w, 3)
+    pos = synth.positions(0, n)
+    u = synth.sample_uniforms(0, n)
+    aux = synth.aux_inputs(0, n) if w.mode == synth.PRODUCT else None
+    for _ in range(args.warmup):
+        oracle.query_sample(w, params, pos[:, :256], u[:, :256], aux[:, :256] if aux is not None else None)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.query_sample(w, params, pos, u, aux)
+    dt = time.perf_counter() - t0
+    v = n * args.steps / dt
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": "guided queries/s (encode+decode+sample+pdf)",
+        "value": v, "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "queries_per_step": n, "sample_of": w.n_query},
+        "cpu_baseline": {"value": v, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{n} queries per step of the {w.n_query}-query workload"},
+        "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(w, seconds_target=10.0):
+    import oracle
+    oracle.build()
+    params = synth.random_params(w, 3)
+    n = 2048
+    pos = synth.positions(1, n)
+    u = synth.sample_uniforms(1, n)
+    aux = synth.aux_inputs(1, n) if w.mode == synth.PRODUCT else None
+    t0 = time.perf_counter()
+    oracle.query_sample(w, params, pos, u, aux)
+    dt = time.perf_counter() - t0
+    reps = max(1, int(seconds_target / max(dt, 1e-3)))
+    reps = min(reps, 64)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.query_sample(w, params, pos, u, aux)
+    dt = time.perf_counter() - t0
+    return {"value": n * reps / dt, "unit": "queries/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{n * reps} queries ({reps} x {n}) of the {w.n_query}-query workload, {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="paper_hash", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--ref-sample", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-train", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_env()
+    w = workload_of(args.workload)
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, w, rank)
+        return
+
+    import torch
+    import paper_2504_04315_gb300 as npm
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    n = w.n_query
+    nrot = 8
+    m = npm.NPM(npm.config_from(w, max_batch=n))
+    params = synth.random_params(w, 3)
+    m.set_params(params)
+    seed0 = 1000 * rank
+    pos = [torch.from_numpy(synth.positions(seed0 + i, n)).cuda() for i in range(nrot)]
+    uu = [torch.from_numpy(synth.sample_uniforms(seed0 + i, n)).cuda() for i in range(nrot)]
+    aux = ([torch.from_numpy(synth.aux_inputs(seed0 + i, n)).cuda() for i in range(nrot)]
+           if w.mode == synth.PRODUCT else [None] * nrot)
+    outs = [(torch.empty((3, n), device="cuda"), torch.empty((n,), device="cuda"))
+            for _ in range(nrot)]
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        k = i % nrot
+        m.query_sample(pos[k], uu[k], aux[k], out=outs[k], stream=stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    K = args.steps
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        evs[0].record(stream)
+        for i in range(K):
+            step(i)
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(K)]
+    total_ms = evs[0].elapsed_time(evs[K])
+    t = torch.tensor([total_ms], device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = n * K * world / (total_ms / 1e3)
+    kern_ms = statistics.mean(per)
+
+    # End to end through the host-buffer entry point: pinned inputs copied
+    # in, results copied out, inside the timed region.
+    hpos = [torch.from_numpy(synth.positions(seed0 + i, n)).pin_memory() for i in range(2)]
+    hu = [torch.from_numpy(synth.sample_uniforms(seed0 + i, n)).pin_memory() for i in range(2)]
+    haux = ([torch.from_numpy(synth.aux_inputs(seed0 + i, n)).pin_memory() for i in range(2)]
+            if w.mode == synth.PRODUCT else [None, None])
+    hd = torch.empty((3, n)).pin_memory()
+    hp = torch.empty((n,)).pin_memory()
+    for i in range(2):
+        m.query_sample_host(hpos[i], hu[i], hd, hp, haux[i], stream=stream)
+    ke = max(4, K // 4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(ke):
+        m.query_sample_host(hpos[i % 2], hu[i % 2], hd, hp, haux[i % 2], stream=stream)
+    e2e_s = time.perf_counter() - t0
+    h2d = n * 4 * (3 + 3 + (7 if w.mode == synth.PRODUCT else 0))
+    d2h = n * 4 * 4
+
+    # Training throughput (samples/s): one npm_train_step per step on the
+    # product-mode workload's batch shape.
+    train = None
+    if not args.no_train:
+        tw = synth.PRODUCT_BF16.with_(precision=synth.FP32)
+        nt = tw.n_train
+        mt = npm.NPM(npm.config_from(tw, max_batch=nt))
+        mt.set_params(synth.random_params(tw, 5))
+        b = synth.train_batch_uniform(tw, nt, seed=5 + rank)
+        tb = [torch.from_numpy(a).cuda() for a in (b.pos, b.dir, b.radiance, b.pdf, b.aux)]
+        loss = torch.zeros(1, device="cuda")
+        for _ in range(3):
+            mt.train_step(tb[0], tb[1], tb[2], tb[3], tb[4], loss_out=loss)
+        torch.cuda.synchronize()
+        kt = max(3, K // 10)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(kt):
+            mt.train_step(tb[0], tb[1], tb[2], tb[3], tb[4], loss_out=loss)
+        e1.record()
+        torch.cuda.synchronize()
+        tms = e0.elapsed_time(e1) / kt
+        train = {"value": nt * world / (tms / 1e3), "unit": "train samples/s", "ms_per_step": tms,
+                 "config": {"workload": tw.name.replace("bf16", "fp32 train kernels"),
+                            "batch": nt, "kernels_per_step": 4}}
+        mt.close()
+
+    if rank != 0:
+        return
+    pk, pk_src = peaks()
+    props = torch.cuda.get_device_properties(local)
+    clocks = clk.summary()
+    sm_max = clocks.get("sm_max_mhz") or pk.get("sm_max_mhz", 2070.0)
+    # FP32 CUDA-core peak: SMs x 128 FP32 lanes x 2 flop x max SM clock.
+    alu_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    achieved = mlp_flops(w) * n / (kern_ms / 1e3) / 1e12
+    per_sorted = sorted(per)
+    line = {
+        "metric": "guided queries/s (encode+decode+sample+pdf)",
+        "value": value, "unit": "queries/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if w.precision == synth.FP32 else "bf16",
+        "data": "synthetic (seeded positions/uniforms; parameters with kappa up to ~35)",
+        "config": {"workload": w.name, "queries_per_step": n,
+                   "l2": f"inputs rotate over {nrot} batches ({nrot * n * 40 / 1e6:.0f} MB incl. outputs) > L2",
+                   "parallelism": f"dp{world} (independent batches per GPU)"},
+        "latency": {"p50_ms": per_sorted[len(per) // 2],
+                    "p99_ms": per_sorted[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)],
+                    "unit": "ms per 2^20-query batch"},
+        "e2e": {"value": n * ke * world / e2e_s, "unit": "queries/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": K,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved / alu_peak, "traffic": None,
+                     "kernel": "k_forward_fp32<sample>",
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"},
+        "clocks": clocks,
+        "train": train,
+        "peaks_source": pk_src,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(line), flush=True)
+    m.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

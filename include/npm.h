@@ -1,0 +1,229 @@
+/*
+ * npm.h -- C ABI of the GB300 (sm_103a) implementation of the hot path of
+ * Neural Parametric Mixtures (NPM) for path guiding (Dong, Wang, Li,
+ * SIGGRAPH 2023).
+ *
+ * What the library computes, per path vertex (a "query"):
+ *   1. G(x): a multi-resolution grid embedding of the position x in [0,1]^3,
+ *      trilinear blending of the 8 corner features on each level, levels
+ *      concatenated (Sec. 5.1, Eq. 11). Levels with D^3 > T are hashed.
+ *   2. In product mode (Sec. 4.3, Eq. 13-14) the network input also holds the
+ *      spherical-harmonics encoding of the outgoing direction (4 bands, 16
+ *      values) and of the normal (2 bands, 4 values) and the roughness.
+ *   3. A bias-free MLP with ReLU hidden layers (Sec. 5.3, Eq. 12) decodes the
+ *      input into 4K raw outputs, mapped per lobe by Table 1 into a K-lobe
+ *      von Mises-Fisher mixture (Eq. 3-4).
+ *   4. The mixture is sampled (Sec. 5.3: numerically stable vMF sampling) and
+ *      its density evaluated (Eq. 4); training minimises the KL divergence to
+ *      the target through its Monte Carlo gradient (Sec. 4.2, Eq. 7-10) with
+ *      Adam (Sec. 5.3).
+ *
+ * Conventions (every entry point):
+ *   - Per-query arrays are structure-of-arrays FP32 with a leading dimension
+ *     ld >= n: component c of query j is at p[c * ld + j]. (Sec. 5.2 keeps
+ *     the wavefront queues in SoA layout.)
+ *   - Array arguments of the hot calls are DEVICE pointers owned by the
+ *     caller unless the name ends in _host. The library never keeps them.
+ *   - The library owns the parameters, the gradient, the Adam moments and a
+ *     workspace sized at npm_create from max_batch; the hot calls allocate
+ *     nothing.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *     default stream). Argument errors are detected on the host and returned
+ *     before anything is launched. A failed launch returns NPM_ERR_CUDA. An
+ *     asynchronous device fault surfaces as NPM_ERR_CUDA on a later call.
+ *   - n == 0 is valid and launches nothing. n > max_batch returns
+ *     NPM_ERR_CAPACITY.
+ *   - Positions outside [0,1]^3 are clamped to the box; direction arguments
+ *     are unit vectors.
+ *   - npm_last_error() returns a thread-local description of the last error.
+ *   - A handle may be used from one host thread at a time.
+ */
+#ifndef NPM_H
+#define NPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NPM_OK = 0,
+    NPM_ERR_INVALID_ARG = 1, /* bad pointer, size, stride or configuration */
+    NPM_ERR_OOM = 2,         /* device allocation failed (npm_create only) */
+    NPM_ERR_CUDA = 3,        /* a CUDA call or kernel launch failed */
+    NPM_ERR_CAPACITY = 4,    /* n > max_batch */
+    NPM_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    NPM_ERR_NUMERIC = 6,     /* non-finite loss: the Adam step was skipped */
+    NPM_ERR_UNSUPPORTED = 7, /* valid but not built (e.g. shape limits) */
+    NPM_ERR_IO = 8           /* npm_save / npm_load file error */
+} npm_status;
+
+enum { NPM_RADIANCE = 0, NPM_PRODUCT = 1 };  /* Sec. 4.1 / Sec. 4.3 */
+enum { NPM_SOFTPLUS = 0, NPM_EXP = 1 };      /* kappa mapping; Table 1 uses exp */
+enum { NPM_FP32 = 0, NPM_BF16 = 1 };         /* MLP / grid arithmetic */
+
+#define NPM_MAX_LEVELS 32
+#define NPM_MAX_LAYERS 8
+#define NPM_MAX_WIDTH 128
+#define NPM_MAX_LOBES 16
+
+/*
+ * Model configuration (all fields explicit, no hidden defaults).
+ *   level_res[l]   D_l, lattice points per axis on level l (D_l >= 2).
+ *   log2_table     T = 2^log2_table entries per hashed level; a level with
+ *                  D_l^3 <= T is stored densely (index i + D (j + D k)),
+ *                  otherwise hashed: (i ^ j*2654435761 ^ k*805459861) mod T.
+ *   widths[0..n_layers]  MLP widths; widths[0] is the network input (grid
+ *                  features, plus 21 SH/roughness values in product mode,
+ *                  zero-padded), widths[n_layers] must equal 4K. Every width
+ *                  is a multiple of 4 and at most NPM_MAX_WIDTH.
+ *   precision      NPM_FP32: FP32 grid and CUDA-core FP32 MLP.
+ *                  NPM_BF16: FP16 grid copy, BF16 tensor-core MLP (tcgen05)
+ *                  with FP32 accumulation; all vMF math stays FP32. Master
+ *                  parameters and Adam state are FP32 in both modes.
+ *   lr, beta1, beta2, eps   Adam (Sec. 5.3 uses lr 0.005).
+ *   max_batch      largest n of any call; sizes the workspace.
+ *   seed           seeds npm_create's parameter initialisation
+ *                  (grid U[-1e-4, 1e-4], MLP Glorot-uniform).
+ */
+typedef struct npm_config {
+    int mode;
+    int n_levels;
+    int feat_per_level;
+    int log2_table;
+    int level_res[NPM_MAX_LEVELS];
+    int n_layers;
+    int widths[NPM_MAX_LAYERS + 1];
+    int K;
+    int kappa_act;
+    int precision;
+    float lr, beta1, beta2, eps;
+    int64_t max_batch;
+    uint64_t seed;
+} npm_config;
+
+typedef struct npm_handle npm_handle;
+
+/* Create a model on the current CUDA device. Parameters start from the
+ * seeded initialisation; replace them with npm_set_params. Errors:
+ * NPM_ERR_INVALID_ARG for an inconsistent config, NPM_ERR_OOM. */
+npm_status npm_create(const npm_config* cfg, npm_handle** out);
+
+/* Free every device buffer of the handle (synchronises the device first).
+ * NULL is a no-op. */
+npm_status npm_destroy(npm_handle* h);
+
+/*
+ * Guided sampling: encode + decode + sample + pdf (Sec. 5.2 steps 1-5).
+ *   pos   [3][ld]  positions x.
+ *   aux   [7][ld]  product mode: wo (3), normal (3), roughness; NULL in
+ *                  radiance mode.
+ *   u     [3][ld]  uniforms in [0,1): u0 picks the lobe against the
+ *                  cumulative weights, u1 the cosine to the lobe mean
+ *                  (inverse CDF), u2 the azimuth. When uniform_frac > 0, u is
+ *                  [4][ld] and u3 < uniform_frac draws the direction
+ *                  uniformly on the sphere from (u1, u2) instead (a
+ *                  one-sample mixture with a BSDF stand-in, Sec. 6.1).
+ *   dir_out  [3][ld]  sampled unit directions.
+ *   pdf_out  [n]      density of the whole strategy at dir_out:
+ *                  uniform_frac/(4 pi) + (1 - uniform_frac) V(dir_out).
+ *   mix_out  [4K][ld] or NULL: decoded mixture, rows (lambda, kappa,
+ *                  theta, phi) per lobe (Table 1).
+ */
+npm_status npm_query_sample(npm_handle* h, int64_t n, const float* pos, const float* aux,
+                            const float* u, int64_t ld, float uniform_frac, float* dir_out,
+                            float* pdf_out, float* mix_out, void* stream);
+
+/* npm_query_sample with every array in HOST memory (pinned memory lets the
+ * copies overlap): the library copies the inputs into its own device staging
+ * buffers (sized by max_batch at npm_create), runs the same kernel in chunks
+ * on two internal streams so that copies and compute overlap, copies dir_out
+ * and pdf_out back, and returns after `stream` has completed the work. The
+ * host arrays use the same [c][ld] layout. */
+npm_status npm_query_sample_host(npm_handle* h, int64_t n, const float* pos, const float* aux,
+                                 const float* u, int64_t ld, float uniform_frac, float* dir_out,
+                                 float* pdf_out, void* stream);
+
+/* Mixture density V(dir | Theta(x)) (Eq. 4) at given unit directions
+ * dir [3][ld]; pdf_out [n]. */
+npm_status npm_eval_pdf(npm_handle* h, int64_t n, const float* pos, const float* aux,
+                        const float* dir, int64_t ld, float* pdf_out, void* stream);
+
+/*
+ * One training step (Sec. 4.2 and 5.3): the loss
+ *   l = -(1/n) sum_j (radiance_j / sample_pdf_j) log V(dir_j | Theta(x_j)),
+ * whose gradient is the Monte Carlo KL gradient of Eq. 9 up to the constant
+ * normalisation of the target; back-propagation through the mapping, the
+ * MLP and the grid (activations recomputed); then one dense Adam step over
+ * all parameters.
+ *   radiance [n]  noisy estimates L_j >= 0; sample_pdf [n] > 0 the density
+ *                 dir_j was drawn from (a constant of the step).
+ *   loss_out      device float or NULL; receives l (written, not added).
+ * The call does not synchronise. If the loss is not finite the Adam kernel
+ * skips the update on the device (parameters and moments unchanged, the step
+ * counter still advances) and records NPM_ERR_NUMERIC in the device status
+ * word, which npm_check_device_status reports.
+ */
+npm_status npm_train_step(npm_handle* h, int64_t n, const float* pos, const float* aux,
+                          const float* dir, const float* radiance, const float* sample_pdf,
+                          int64_t ld, float* loss_out, void* stream);
+
+/* Gradient only: zero the gradient buffer, then accumulate
+ * d/dparams of sum_j dlogv_j log V(dir_j | Theta(x_j)) into it.
+ * dlogv [n] are the per-query upstream weights (npm_train_step uses
+ * -radiance/(n sample_pdf)). */
+npm_status npm_backward(npm_handle* h, int64_t n, const float* pos, const float* aux,
+                        const float* dir, const float* dlogv, int64_t ld, void* stream);
+
+/* One dense Adam step (with bias correction) from the gradient buffer;
+ * clears the gradient. */
+npm_status npm_adam_step(npm_handle* h, void* stream);
+
+/* ------------------------------------------------------------ support */
+
+/* Number of FP32 parameters: grid (level, entry, feature), then each weight
+ * matrix row-major [out][in]. */
+int64_t npm_num_params(const npm_handle* h);
+
+/* Copy parameters from / to a HOST FP32 buffer of npm_num_params values.
+ * set also refreshes the reduced-precision copies and resets nothing else.
+ * Both synchronise the device. */
+npm_status npm_set_params(npm_handle* h, const float* host, int64_t count);
+npm_status npm_get_params(npm_handle* h, float* host, int64_t count);
+/* Copy the gradient buffer to a HOST buffer (it holds the result of the last
+ * npm_backward; npm_adam_step and npm_train_step leave it zeroed). */
+npm_status npm_get_grads(npm_handle* h, float* host, int64_t count);
+
+/* Device pointers to the FP32 master parameters and gradient (owned by the
+ * handle, valid until npm_destroy). */
+float* npm_params_device(npm_handle* h);
+float* npm_grads_device(npm_handle* h);
+
+/* Adam state: step counter and moments (host buffers of npm_num_params). */
+npm_status npm_get_adam(npm_handle* h, int* step, float* m_host, float* v_host);
+npm_status npm_set_adam(npm_handle* h, int step, const float* m_host, const float* v_host);
+
+/* Grid indices for the bit-exact check: out [L][8][n] int32 (level,
+ * corner with bit0=+x bit1=+y bit2=+z, query), device pointer. */
+npm_status npm_grid_indices(npm_handle* h, int64_t n, const float* pos, int64_t ld,
+                            int32_t* out, void* stream);
+
+/* Checkpoint: configuration, parameters, Adam moments and step counter in a
+ * binary file. npm_load requires a handle created with the same
+ * configuration. */
+npm_status npm_save(npm_handle* h, const char* path);
+npm_status npm_load(npm_handle* h, const char* path);
+
+/* Reads and clears the device-side status word (non-finite loss, bounded
+ * wait timeouts). Synchronises the stream. */
+npm_status npm_check_device_status(npm_handle* h, void* stream);
+
+/* Thread-local text of the last error returned on this thread. */
+const char* npm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NPM_H */

@@ -1,0 +1,232 @@
+"""GB300-native hot path of Neural Parametric Mixtures (NPM) for path guiding.
+
+The compute runs in hand-written sm_103a CUDA kernels behind the C ABI of
+``include/npm.h``; this module only marshals torch tensors (device memory and
+streams) into those calls. See ``NPM`` for the entry points.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _lib
+from ._build import build  # noqa: F401
+from ._lib import NpmError  # noqa: F401
+
+RADIANCE, PRODUCT = 0, 1
+SOFTPLUS, EXP = 0, 1
+FP32, BF16 = 0, 1
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def make_config(mode: int, level_res: Sequence[int], feat: int, log2_table: int,
+                widths: Sequence[int], K: int, kappa_act: int = SOFTPLUS,
+                precision: int = FP32, lr: float = 5e-3, beta1: float = 0.9,
+                beta2: float = 0.99, eps: float = 1e-8, max_batch: int = 1 << 20,
+                seed: int = 0) -> _lib.NpmConfig:
+    c = _lib.NpmConfig()
+    c.mode = mode
+    c.n_levels = len(level_res)
+    c.feat_per_level = feat
+    c.log2_table = log2_table
+    for i, r in enumerate(level_res):
+        c.level_res[i] = int(r)
+    c.n_layers = len(widths) - 1
+    for i, w in enumerate(widths):
+        c.widths[i] = int(w)
+    c.K = K
+    c.kappa_act = kappa_act
+    c.precision = precision
+    c.lr, c.beta1, c.beta2, c.eps = lr, beta1, beta2, eps
+    c.max_batch = int(max_batch)
+    c.seed = int(seed)
+    return c
+
+
+def config_from(w, max_batch: Optional[int] = None, precision: Optional[int] = None,
+                seed: int = 0) -> _lib.NpmConfig:
+    """Config from any object with the fields of a workload description
+    (mode, level_res, feat, log2_table, widths, K, kappa_act, precision, lr,
+    beta1, beta2, eps, n_query, n_train)."""
+    mb = max_batch if max_batch is not None else max(w.n_query, w.n_train, 1)
+    return make_config(w.mode, w.level_res, w.feat, w.log2_table, w.widths, w.K, w.kappa_act,
+                       w.precision if precision is None else precision, w.lr, w.beta1, w.beta2,
+                       w.eps, mb, seed)
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        torch = _torch()
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream
+
+
+def _soa(t, rows: int, name: str):
+    """Validate a [rows][ld] float32 CUDA tensor; returns ld."""
+    torch = _torch()
+    if t.dtype != torch.float32 or not t.is_cuda:
+        raise TypeError(f"{name} must be a float32 CUDA tensor")
+    if t.dim() != 2 or t.shape[0] < rows or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous [{rows}][ld] tensor")
+    return t.shape[1]
+
+
+class NPM:
+    """One NPM model on the current CUDA device (library-owned parameters,
+    gradient and Adam state)."""
+
+    def __init__(self, config: _lib.NpmConfig):
+        self._L = _lib.load()
+        self.config = config
+        h = C.c_void_p()
+        _lib.check(self._L.npm_create(C.byref(config), C.byref(h)), "npm_create")
+        self._h = h
+        self.K = config.K
+        self.mode = config.mode
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.npm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- hot path
+    def query_sample(self, pos, u, aux=None, uniform_frac: float = 0.0, n: Optional[int] = None,
+                     want_mix: bool = False, out=None, stream=None):
+        """Guided directions and densities. pos [3][ld], u [3 or 4][ld],
+        aux [7][ld] (product mode). Returns (dir [3][ld], pdf [ld], mix)."""
+        torch = _torch()
+        ld = _soa(pos, 3, "pos")
+        n = ld if n is None else n
+        _soa(u, 4 if uniform_frac > 0 else 3, "u")
+        if aux is not None:
+            _soa(aux, 7, "aux")
+        if out is None:
+            d = torch.empty((3, ld), device=pos.device, dtype=torch.float32)
+            p = torch.empty((ld,), device=pos.device, dtype=torch.float32)
+        else:
+            d, p = out
+        m = torch.empty((4 * self.K, ld), device=pos.device, dtype=torch.float32) if want_mix else None
+        _lib.check(self._L.npm_query_sample(self._h, n, _ptr(pos), _ptr(aux), _ptr(u), ld,
+                                            float(uniform_frac), _ptr(d), _ptr(p), _ptr(m),
+                                            _stream_ptr(stream)), "npm_query_sample")
+        return d, p, m
+
+    def query_sample_host(self, pos, u, dir_out, pdf_out, aux=None, uniform_frac: float = 0.0,
+                          n: Optional[int] = None, stream=None):
+        """Same as query_sample with all arrays in (preferably pinned) HOST
+        memory -- torch CPU tensors; copies run inside the library."""
+        ld = pos.shape[1]
+        n = ld if n is None else n
+        for t in (pos, u, dir_out, pdf_out) + ((aux,) if aux is not None else ()):
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError("host tensors must be contiguous CPU tensors")
+        _lib.check(self._L.npm_query_sample_host(self._h, n, _ptr(pos), _ptr(aux), _ptr(u), ld,
+                                                 float(uniform_frac), _ptr(dir_out),
+                                                 _ptr(pdf_out), _stream_ptr(stream)),
+                   "npm_query_sample_host")
+
+    def eval_pdf(self, pos, dirs, aux=None, n: Optional[int] = None, out=None, stream=None):
+        torch = _torch()
+        ld = _soa(pos, 3, "pos")
+        n = ld if n is None else n
+        _soa(dirs, 3, "dir")
+        p = torch.empty((ld,), device=pos.device, dtype=torch.float32) if out is None else out
+        _lib.check(self._L.npm_eval_pdf(self._h, n, _ptr(pos), _ptr(aux), _ptr(dirs), ld, _ptr(p),
+                                        _stream_ptr(stream)), "npm_eval_pdf")
+        return p
+
+    def train_step(self, pos, dirs, radiance, sample_pdf, aux=None, n: Optional[int] = None,
+                   loss_out=None, stream=None):
+        torch = _torch()
+        ld = _soa(pos, 3, "pos")
+        n = ld if n is None else n
+        loss = torch.zeros((1,), device=pos.device, dtype=torch.float32) if loss_out is None else loss_out
+        _lib.check(self._L.npm_train_step(self._h, n, _ptr(pos), _ptr(aux), _ptr(dirs),
+                                          _ptr(radiance), _ptr(sample_pdf), ld, _ptr(loss),
+                                          _stream_ptr(stream)), "npm_train_step")
+        return loss
+
+    def backward(self, pos, dirs, dlogv, aux=None, n: Optional[int] = None, stream=None):
+        ld = _soa(pos, 3, "pos")
+        n = ld if n is None else n
+        _lib.check(self._L.npm_backward(self._h, n, _ptr(pos), _ptr(aux), _ptr(dirs), _ptr(dlogv),
+                                        ld, _stream_ptr(stream)), "npm_backward")
+
+    def adam_step(self, stream=None):
+        _lib.check(self._L.npm_adam_step(self._h, _stream_ptr(stream)), "npm_adam_step")
+
+    # -- support
+    def num_params(self) -> int:
+        return int(self._L.npm_num_params(self._h))
+
+    def set_params(self, params: np.ndarray):
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        _lib.check(self._L.npm_set_params(self._h, a.ctypes.data_as(C.c_void_p), a.size),
+                   "npm_set_params")
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.num_params(), dtype=np.float32)
+        _lib.check(self._L.npm_get_params(self._h, a.ctypes.data_as(C.c_void_p), a.size),
+                   "npm_get_params")
+        return a
+
+    def get_grads(self) -> np.ndarray:
+        a = np.empty(self.num_params(), dtype=np.float32)
+        _lib.check(self._L.npm_get_grads(self._h, a.ctypes.data_as(C.c_void_p), a.size),
+                   "npm_get_grads")
+        return a
+
+    def get_adam(self):
+        n = self.num_params()
+        m = np.empty(n, dtype=np.float32)
+        v = np.empty(n, dtype=np.float32)
+        step = C.c_int()
+        _lib.check(self._L.npm_get_adam(self._h, C.byref(step), m.ctypes.data_as(C.c_void_p),
+                                        v.ctypes.data_as(C.c_void_p)), "npm_get_adam")
+        return step.value, m, v
+
+    def set_adam(self, step: int, m: np.ndarray, v: np.ndarray):
+        m = np.ascontiguousarray(m, dtype=np.float32)
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        _lib.check(self._L.npm_set_adam(self._h, int(step), m.ctypes.data_as(C.c_void_p),
+                                        v.ctypes.data_as(C.c_void_p)), "npm_set_adam")
+
+    def grid_indices(self, pos, n: Optional[int] = None, stream=None):
+        torch = _torch()
+        ld = _soa(pos, 3, "pos")
+        n = ld if n is None else n
+        out = torch.empty((self.config.n_levels, 8, n), device=pos.device, dtype=torch.int32)
+        _lib.check(self._L.npm_grid_indices(self._h, n, _ptr(pos), ld, _ptr(out),
+                                            _stream_ptr(stream)), "npm_grid_indices")
+        return out
+
+    def save(self, path: str):
+        _lib.check(self._L.npm_save(self._h, path.encode()), "npm_save")
+
+    def load(self, path: str):
+        _lib.check(self._L.npm_load(self._h, path.encode()), "npm_load")
+
+    def check_device_status(self, stream=None):
+        _lib.check(self._L.npm_check_device_status(self._h, _stream_ptr(stream)),
+                   "npm_check_device_status")

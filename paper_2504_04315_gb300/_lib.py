@@ -1,0 +1,95 @@
+"""ctypes view of the C ABI declared in include/npm.h.
+
+Loading fails loudly (RuntimeError) when the CUDA library has not been
+built: there is no CPU fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from ._build import LIB
+
+MAX_LEVELS = 32
+MAX_LAYERS = 8
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_NUMERIC, \
+    ERR_UNSUPPORTED, ERR_IO = range(9)
+STATUS_NAMES = ["NPM_OK", "NPM_ERR_INVALID_ARG", "NPM_ERR_OOM", "NPM_ERR_CUDA",
+                "NPM_ERR_CAPACITY", "NPM_ERR_TIMEOUT", "NPM_ERR_NUMERIC",
+                "NPM_ERR_UNSUPPORTED", "NPM_ERR_IO"]
+
+
+class NpmConfig(C.Structure):
+    _fields_ = [
+        ("mode", C.c_int), ("n_levels", C.c_int), ("feat_per_level", C.c_int),
+        ("log2_table", C.c_int), ("level_res", C.c_int * MAX_LEVELS),
+        ("n_layers", C.c_int), ("widths", C.c_int * (MAX_LAYERS + 1)), ("K", C.c_int),
+        ("kappa_act", C.c_int), ("precision", C.c_int),
+        ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+        ("max_batch", C.c_int64), ("seed", C.c_uint64),
+    ]
+
+
+vp = C.c_void_p
+i64 = C.c_int64
+f32 = C.c_float
+st = C.c_int
+
+# name -> (restype, argtypes); every symbol include/npm.h declares.
+SIGNATURES = {
+    "npm_create": (st, [C.POINTER(NpmConfig), C.POINTER(vp)]),
+    "npm_destroy": (st, [vp]),
+    "npm_query_sample": (st, [vp, i64, vp, vp, vp, i64, f32, vp, vp, vp, vp]),
+    "npm_query_sample_host": (st, [vp, i64, vp, vp, vp, i64, f32, vp, vp, vp]),
+    "npm_eval_pdf": (st, [vp, i64, vp, vp, vp, i64, vp, vp]),
+    "npm_train_step": (st, [vp, i64, vp, vp, vp, vp, vp, i64, vp, vp]),
+    "npm_backward": (st, [vp, i64, vp, vp, vp, vp, i64, vp]),
+    "npm_adam_step": (st, [vp, vp]),
+    "npm_num_params": (i64, [vp]),
+    "npm_set_params": (st, [vp, vp, i64]),
+    "npm_get_params": (st, [vp, vp, i64]),
+    "npm_get_grads": (st, [vp, vp, i64]),
+    "npm_params_device": (vp, [vp]),
+    "npm_grads_device": (vp, [vp]),
+    "npm_get_adam": (st, [vp, C.POINTER(C.c_int), vp, vp]),
+    "npm_set_adam": (st, [vp, C.c_int, vp, vp]),
+    "npm_grid_indices": (st, [vp, i64, vp, i64, vp, vp]),
+    "npm_save": (st, [vp, C.c_char_p]),
+    "npm_load": (st, [vp, C.c_char_p]),
+    "npm_check_device_status": (st, [vp, vp]),
+    "npm_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load():
+    """The loaded library (ctypes.CDLL) with typed entry points."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise RuntimeError(
+            "libnpm_gb300.so is not built; run paper_2504_04315_gb300._build.build() "
+            "(or __graft_entry__.build()). There is no CPU fallback.")
+    lib = C.CDLL(LIB)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class NpmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = load().npm_last_error().decode(errors="replace")
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{where}: {name}: {msg}")
+        self.status = status
+
+
+def check(status: int, where: str) -> None:
+    if status != OK:
+        raise NpmError(status, where)

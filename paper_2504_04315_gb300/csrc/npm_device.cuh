@@ -1,0 +1,235 @@
+// npm_device.cuh -- device-side configuration and per-query math of the NPM
+// hot path: grid lattice index and trilinear weights (Sec. 5.1, Eq. 11),
+// spherical-harmonics encoding (Sec. 4.3), the Table 1 output mapping, the vMF
+// mixture density (Eq. 3-4) and vMF sampling (Sec. 5.3).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "npm.h"
+
+namespace npm {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kInv4Pi = 0.0795774715459476679f;
+
+// Everything a kernel needs to know about the model, passed by value.
+struct DevCfg {
+    int mode;        // NPM_RADIANCE / NPM_PRODUCT
+    int n_levels;
+    int feat;        // F
+    int K;           // lobes
+    int kappa_act;   // NPM_SOFTPLUS / NPM_EXP
+    int n_layers;
+    int grid_feats;  // n_levels * feat
+    uint32_t table_mask;  // T - 1
+    uint32_t dense_mask;  // bit l: level l is stored densely
+    int widths[NPM_MAX_LAYERS + 1];
+    int level_res[NPM_MAX_LEVELS];
+    uint32_t level_off[NPM_MAX_LEVELS];  // first entry of each level
+    // FP32 fused kernels: per layer, padded output count (multiple of 16)
+    // and float offsets of the pre-arranged weight blobs.
+    int np_fwd[NPM_MAX_LAYERS];   // padded N of W^T [K][np] (forward)
+    int np_bwd[NPM_MAX_LAYERS];   // padded K of W [N][np] (backward)
+    int off_fwd[NPM_MAX_LAYERS];
+    int off_bwd[NPM_MAX_LAYERS];
+    int fwd_floats, bwd_floats;
+    int max_width;
+};
+
+// ------------------------------------------------------ lattice (Eq. 11)
+
+// Cell and fraction along one axis: x clamped to [0,1] (NaN -> 0),
+// p = x * (D - 1) with one round-to-nearest multiply, cell = min(floor p, D-2).
+__device__ __forceinline__ void lattice_axis(float x, int D, uint32_t& cell, float& frac) {
+    float xa = fminf(fmaxf(x, 0.0f), 1.0f);
+    float p = __fmul_rn(xa, (float)(D - 1));
+    int c = (int)floorf(p);
+    c = c > D - 2 ? D - 2 : c;
+    cell = (uint32_t)c;
+    frac = __fsub_rn(p, (float)c);
+}
+
+__device__ __forceinline__ uint32_t lattice_index(const DevCfg& cfg, int l, uint32_t i, uint32_t j,
+                                                  uint32_t k) {
+    if ((cfg.dense_mask >> l) & 1u) {
+        uint32_t D = (uint32_t)cfg.level_res[l];
+        return i + D * (j + D * k);
+    }
+    return (i ^ (j * 2654435761u) ^ (k * 805459861u)) & cfg.table_mask;
+}
+
+// Corner c (bit0 = +x, bit1 = +y, bit2 = +z): entry index and weight.
+struct Cell {
+    uint32_t c[3];
+    float f[3];
+};
+
+__device__ __forceinline__ Cell make_cell(float x, float y, float z, int D) {
+    Cell cl;
+    lattice_axis(x, D, cl.c[0], cl.f[0]);
+    lattice_axis(y, D, cl.c[1], cl.f[1]);
+    lattice_axis(z, D, cl.c[2], cl.f[2]);
+    return cl;
+}
+
+__device__ __forceinline__ float corner_weight(const Cell& cl, int corner) {
+    float wx = (corner & 1) ? cl.f[0] : 1.0f - cl.f[0];
+    float wy = (corner & 2) ? cl.f[1] : 1.0f - cl.f[1];
+    float wz = (corner & 4) ? cl.f[2] : 1.0f - cl.f[2];
+    return wx * wy * wz;
+}
+
+__device__ __forceinline__ uint32_t corner_index(const DevCfg& cfg, int l, const Cell& cl,
+                                                 int corner) {
+    return lattice_index(cfg, l, cl.c[0] + (corner & 1), cl.c[1] + ((corner >> 1) & 1),
+                         cl.c[2] + ((corner >> 2) & 1));
+}
+
+// ------------------------------------------ spherical harmonics (Sec. 4.3)
+
+// Real orthonormal SH, bands 0..3 (16 values), in the order
+// l=0; l=1: y, z, x; l=2: xy, yz, 3z^2-1, xz, x^2-y^2; l=3: m=-3..3.
+__device__ __forceinline__ void sh_band4(float x, float y, float z, float* o) {
+    const float c0 = 0.28209479177387814f;
+    const float c1 = 0.48860251190291992f;
+    const float c2a = 1.09254843059207907f;   // sqrt(15/pi)/2
+    const float c2b = 0.31539156525252001f;   // sqrt(5/pi)/4
+    const float c2c = 0.54627421529603959f;   // sqrt(15/pi)/4
+    const float c3a = 0.59004358992664352f;   // sqrt(35/(2pi))/4
+    const float c3b = 2.89061144264055405f;   // sqrt(105/pi)/2
+    const float c3c = 0.45704579946446573f;   // sqrt(21/(2pi))/4
+    const float c3d = 0.37317633259011539f;   // sqrt(7/pi)/4
+    const float c3e = 1.44530572132027702f;   // sqrt(105/pi)/4
+    float xx = x * x, yy = y * y, zz = z * z;
+    o[0] = c0;
+    o[1] = c1 * y;
+    o[2] = c1 * z;
+    o[3] = c1 * x;
+    o[4] = c2a * x * y;
+    o[5] = c2a * y * z;
+    o[6] = c2b * (3.0f * zz - 1.0f);
+    o[7] = c2a * x * z;
+    o[8] = c2c * (xx - yy);
+    o[9] = c3a * y * (3.0f * xx - yy);
+    o[10] = c3b * x * y * z;
+    o[11] = c3c * y * (5.0f * zz - 1.0f);
+    o[12] = c3d * z * (5.0f * zz - 3.0f);
+    o[13] = c3c * x * (5.0f * zz - 1.0f);
+    o[14] = c3e * z * (xx - yy);
+    o[15] = c3a * x * (xx - 3.0f * yy);
+}
+
+__device__ __forceinline__ void sh_band2(float x, float y, float z, float* o) {
+    o[0] = 0.28209479177387814f;
+    o[1] = 0.48860251190291992f * y;
+    o[2] = 0.48860251190291992f * z;
+    o[3] = 0.48860251190291992f * x;
+}
+
+// ------------------------------------------------ Table 1 output mapping
+
+__device__ __forceinline__ float logistic(float t) { return 1.0f / (1.0f + expf(-t)); }
+
+__device__ __forceinline__ float softplus(float t) {
+    return t > 0.0f ? t + log1pf(expf(-t)) : log1pf(expf(t));
+}
+
+struct Lobe {
+    float lam, kap, mu[3];
+};
+
+// kappa and mean direction of one lobe from its raw outputs
+// (kappa', theta', phi'); theta = pi s(theta'), phi = 2 pi s(phi').
+__device__ __forceinline__ void decode_lobe(int kappa_act, float rk, float rt, float rp, Lobe& L,
+                                            float* theta, float* phi) {
+    L.kap = kappa_act == NPM_EXP ? expf(rk) : softplus(rk);
+    float th = kPi * logistic(rt);
+    float ph = 2.0f * kPi * logistic(rp);
+    float st, ct, sp, cp;
+    sincosf(th, &st, &ct);
+    sincosf(ph, &sp, &cp);
+    L.mu[0] = st * cp;
+    L.mu[1] = st * sp;
+    L.mu[2] = ct;
+    if (theta) *theta = th;
+    if (phi) *phi = ph;
+}
+
+// ------------------------------------------------------ vMF (Eq. 3-4)
+
+// kappa / (4 pi sinh kappa) * e^kappa, written kappa / (2 pi (1 - e^{-2 kappa}))
+// so that it pairs with exp(kappa (mu.w - 1)) without overflow.
+__device__ __forceinline__ float vmf_scaled_norm(float k) {
+    if (k < 1e-6f) return (1.0f + k) * kInv4Pi;
+    return k / (2.0f * kPi * (-expm1f(-2.0f * k)));
+}
+
+__device__ __forceinline__ float vmf_eval(const Lobe& L, float cn, float wx, float wy, float wz) {
+    float d = L.mu[0] * wx + L.mu[1] * wy + L.mu[2] * wz;
+    return cn * expf(L.kap * (d - 1.0f));
+}
+
+// One minus the cosine to the mean, t = 1 - W, by inversion of the vMF
+// cosine CDF in the stable log1p / expm1 form (Jakob 2012). Returning t
+// rather than W keeps sin(angle) = sqrt(t (2 - t)) accurate for samples very
+// close to the mean.
+__device__ __forceinline__ float vmf_sample_t(float k, float u1) {
+    if (!(k > 1e-20f)) return 2.0f * u1;
+    float t = -log1pf(u1 * expm1f(-2.0f * k)) / k;
+    return fminf(fmaxf(t, 0.0f), 2.0f);
+}
+
+// Orthonormal basis (t, b) completing unit vector n (Duff et al. 2017).
+__device__ __forceinline__ void frame(const float n[3], float t[3], float b[3]) {
+    float sg = n[2] >= 0.0f ? 1.0f : -1.0f;
+    float a = -1.0f / (sg + n[2]);
+    float bb = n[0] * n[1] * a;
+    t[0] = 1.0f + sg * n[0] * n[0] * a;
+    t[1] = sg * bb;
+    t[2] = -sg * n[0];
+    b[0] = bb;
+    b[1] = sg + n[1] * n[1] * a;
+    b[2] = -n[1];
+}
+
+__device__ __forceinline__ void vmf_sample(const Lobe& L, float u1, float u2, float out[3]) {
+    const float t1 = vmf_sample_t(L.kap, u1);
+    const float W = 1.0f - t1;
+    const float s = sqrtf(t1 * (2.0f - t1));
+    float sp, cp;
+    sincosf(2.0f * kPi * u2, &sp, &cp);
+    float lx = s * cp, ly = s * sp;
+    float t[3], b[3];
+    frame(L.mu, t, b);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out[a] = lx * t[a] + ly * b[a] + W * L.mu[a];
+}
+
+__device__ __forceinline__ void uniform_sphere(float u1, float u2, float out[3]) {
+    float z = 1.0f - 2.0f * u1;
+    float r = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+    float sp, cp;
+    sincosf(2.0f * kPi * u2, &sp, &cp);
+    out[0] = r * cp;
+    out[1] = r * sp;
+    out[2] = z;
+}
+
+// 1/k - coth k (derivative of log(k / sinh k)). Below 0.25 its Laurent series
+// -k/3 + k^3/45 - 2k^5/945 + k^7/4725 avoids the cancellation of the direct
+// form (truncation < 1e-10 there).
+__device__ __forceinline__ float inv_minus_coth(float k) {
+    if (k < 0.25f) {
+        float k2 = k * k;
+        return k * (-1.0f / 3.0f + k2 * (1.0f / 45.0f + k2 * (-2.0f / 945.0f + k2 * (1.0f / 4725.0f))));
+    }
+    // coth k = 1 + 2 / (e^{2k} - 1)
+    return 1.0f / k - 1.0f - 2.0f / expm1f(2.0f * k);
+}
+
+// Device status word bits (read and cleared by npm_check_device_status).
+enum : int { kStatusNumeric = 1, kStatusTimeout = 2 };
+
+}  // namespace npm

@@ -1,0 +1,785 @@
+// npm_fp32.cu -- FP32 CUDA-core path of the NPM hot path.
+//
+// One persistent CTA of 128 threads walks 64-query tiles. Per tile:
+//   encode  : 2 threads per query gather the 8 corners of every level and
+//             blend them (Sec. 5.1, Eq. 11); product mode appends the SH
+//             encodings and the roughness (Sec. 4.3).
+//   MLP     : each layer is a 64 x N x K tile GEMM from shared memory; thread
+//             (qg, g) owns queries qg + 8j (j < 8) and outputs g*NI .. g*NI+NI-1
+//             (Sec. 5.3, Eq. 12). Weights are staged once per CTA.
+//   epilogue: 2 threads per query (lobes split in halves, combined with
+//             warp shuffles) map the raw outputs (Table 1), then sample and/or
+//             evaluate the mixture (Eq. 3-4).
+// The training kernel recomputes the forward pass, forms the gradient of the
+// weighted log-likelihood in the log domain (Eq. 9), back-propagates through
+// the layers and scatters grid gradients with vector atomics.
+#include <math.h>
+
+#include "npm_device.cuh"
+#include "npm_kernels.h"
+
+namespace npm {
+
+constexpr int kTQ = 64;   // queries per tile
+constexpr int kNT = 128;  // threads per CTA
+constexpr unsigned kFull = 0xffffffffu;
+
+// ----------------------------------------------------------- tile GEMM
+
+template <int NI>
+__device__ __forceinline__ void load_w(const float* p, float (&w)[NI]) {
+    if constexpr (NI == 1) {
+        w[0] = p[0];
+    } else if constexpr (NI == 2) {
+        float2 v = *reinterpret_cast<const float2*>(p);
+        w[0] = v.x;
+        w[1] = v.y;
+    } else {
+#pragma unroll
+        for (int c = 0; c < NI; c += 4) {
+            float4 v = *reinterpret_cast<const float4*>(p + c);
+            w[c] = v.x;
+            w[c + 1] = v.y;
+            w[c + 2] = v.z;
+            w[c + 3] = v.w;
+        }
+    }
+}
+
+// out[q][n] = f(sum_k in[q][k] * WT[k][n]) for q < 64, n < N. WT rows are
+// padded to NP = 16 * NI columns (zeros beyond N). mode 0: identity,
+// 1: ReLU, 2: keep where mask[q][n] > 0 (ReLU derivative), else 0.
+template <int NI>
+__device__ __forceinline__ void tile_gemm(const float* __restrict__ in, int AS, int K,
+                                          const float* __restrict__ WT, int NP,
+                                          float* __restrict__ out, int N, int mode,
+                                          const float* __restrict__ mask) {
+    const int t = threadIdx.x;
+    const int g = t & 15, qg = t >> 4;
+    float acc[8][NI];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int i = 0; i < NI; ++i) acc[j][i] = 0.0f;
+    for (int k = 0; k < K; k += 4) {
+        float4 a[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = *reinterpret_cast<const float4*>(in + (qg + 8 * j) * AS + k);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            float w[NI];
+            load_w<NI>(WT + (k + kk) * NP + g * NI, w);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                float av = kk == 0 ? a[j].x : kk == 1 ? a[j].y : kk == 2 ? a[j].z : a[j].w;
+#pragma unroll
+                for (int i = 0; i < NI; ++i) acc[j][i] = fmaf(av, w[i], acc[j][i]);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int row = (qg + 8 * j) * AS;
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int n = g * NI + i;
+            if (n < N) {
+                float v = acc[j][i];
+                if (mode == 1) v = fmaxf(v, 0.0f);
+                if (mode == 2) v = mask[row + n] > 0.0f ? v : 0.0f;
+                out[row + n] = v;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void layer(const float* in, int AS, int K, const float* WT, int NP,
+                                      float* out, int N, int mode, const float* mask) {
+    switch (NP) {
+        case 16: tile_gemm<1>(in, AS, K, WT, NP, out, N, mode, mask); break;
+        case 32: tile_gemm<2>(in, AS, K, WT, NP, out, N, mode, mask); break;
+        case 64: tile_gemm<4>(in, AS, K, WT, NP, out, N, mode, mask); break;
+        default: tile_gemm<8>(in, AS, K, WT, NP, out, N, mode, mask); break;
+    }
+}
+
+// ------------------------------------------------------------- encode
+
+// Fills act[q][0 .. widths[0]) for the tile's 64 queries.
+__device__ __forceinline__ void encode_tile(const DevCfg& cfg, const float* __restrict__ grid,
+                                            int64_t base, int64_t n, int64_t ld,
+                                            const float* __restrict__ pos,
+                                            const float* __restrict__ aux, float* act, int AS) {
+    const int t = threadIdx.x;
+    const int q = t & (kTQ - 1), part = t >> 6;
+    const int64_t j = base + q;
+    const bool valid = j < n;
+    float x = 0.0f, y = 0.0f, z = 0.0f;
+    if (valid) {
+        x = pos[j];
+        y = pos[ld + j];
+        z = pos[2 * ld + j];
+    }
+    float* row = act + q * AS;
+    const int F = cfg.feat;
+    for (int l = part; l < cfg.n_levels; l += 2) {
+        const Cell cl = make_cell(x, y, z, cfg.level_res[l]);
+        const float* gl = grid + (size_t)cfg.level_off[l] * F;
+        float s[8];
+#pragma unroll
+        for (int f = 0; f < 8; ++f) s[f] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float w = corner_weight(cl, c);
+            const float* e = gl + (size_t)corner_index(cfg, l, cl, c) * F;
+            if (F == 2) {
+                float2 v = __ldg(reinterpret_cast<const float2*>(e));
+                s[0] += w * v.x;
+                s[1] += w * v.y;
+            } else if (F == 4) {
+                float4 v = __ldg(reinterpret_cast<const float4*>(e));
+                s[0] += w * v.x;
+                s[1] += w * v.y;
+                s[2] += w * v.z;
+                s[3] += w * v.w;
+            } else {
+#pragma unroll
+                for (int f = 0; f < 8; ++f)
+                    if (f < F) s[f] += w * __ldg(e + f);
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < 8; ++f)
+            if (f < F) row[l * F + f] = s[f];
+    }
+    const int o = cfg.grid_feats;
+    const int w0 = cfg.widths[0];
+    if (cfg.mode == NPM_PRODUCT) {
+        if (part == 0) {
+            float wo[3] = {0.0f, 0.0f, 1.0f};
+            if (valid) {
+                wo[0] = aux[j];
+                wo[1] = aux[ld + j];
+                wo[2] = aux[2 * ld + j];
+            }
+            float sh[16];
+            sh_band4(wo[0], wo[1], wo[2], sh);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) row[o + i] = sh[i];
+        } else {
+            float nn[3] = {0.0f, 0.0f, 1.0f}, r = 0.0f;
+            if (valid) {
+                nn[0] = aux[3 * ld + j];
+                nn[1] = aux[4 * ld + j];
+                nn[2] = aux[5 * ld + j];
+                r = aux[6 * ld + j];
+            }
+            float sh[4];
+            sh_band2(nn[0], nn[1], nn[2], sh);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) row[o + 16 + i] = sh[i];
+            row[o + 20] = r;
+            for (int i = o + 21; i < w0; ++i) row[i] = 0.0f;
+        }
+    } else if (part == 1) {
+        for (int i = o; i < w0; ++i) row[i] = 0.0f;
+    }
+}
+
+// -------------------------------------------------------- vMF epilogue
+
+// Mapping of one half of the lobes of query q (Table 1). Returns the local
+// lobe count; lam holds normalised weights.
+struct HalfMix {
+    Lobe lob[NPM_MAX_LOBES / 2];
+    float cn[NPM_MAX_LOBES / 2];
+    int l0, cnt;
+};
+
+__device__ __forceinline__ void decode_half(const DevCfg& cfg, const float* raw, int half,
+                                            HalfMix& hm, float* mix_out, int64_t ld, int64_t j,
+                                            bool valid) {
+    const int K = cfg.K, KH = (K + 1) >> 1;
+    hm.l0 = half * KH;
+    hm.cnt = min(K, hm.l0 + KH) - hm.l0;
+    float mx = -INFINITY;
+#pragma unroll
+    for (int ii = 0; ii < NPM_MAX_LOBES / 2; ++ii)
+        if (ii < hm.cnt) mx = fmaxf(mx, raw[4 * (hm.l0 + ii)]);
+    mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, 1));
+    float ssum = 0.0f;
+#pragma unroll
+    for (int ii = 0; ii < NPM_MAX_LOBES / 2; ++ii)
+        if (ii < hm.cnt) {
+            hm.lob[ii].lam = expf(raw[4 * (hm.l0 + ii)] - mx);
+            ssum += hm.lob[ii].lam;
+        }
+    ssum += __shfl_xor_sync(kFull, ssum, 1);
+    const float inv = 1.0f / ssum;
+#pragma unroll
+    for (int ii = 0; ii < NPM_MAX_LOBES / 2; ++ii)
+        if (ii < hm.cnt) {
+            const int i = hm.l0 + ii;
+            hm.lob[ii].lam *= inv;
+            float th, ph;
+            decode_lobe(cfg.kappa_act, raw[4 * i + 1], raw[4 * i + 2], raw[4 * i + 3], hm.lob[ii],
+                        &th, &ph);
+            hm.cn[ii] = vmf_scaled_norm(hm.lob[ii].kap);
+            if (mix_out && valid) {
+                mix_out[(4 * i + 0) * ld + j] = hm.lob[ii].lam;
+                mix_out[(4 * i + 1) * ld + j] = hm.lob[ii].kap;
+                mix_out[(4 * i + 2) * ld + j] = th;
+                mix_out[(4 * i + 3) * ld + j] = ph;
+            }
+        }
+}
+
+__device__ __forceinline__ float half_pdf(const HalfMix& hm, const float w[3]) {
+    float pv = 0.0f;
+#pragma unroll
+    for (int ii = 0; ii < NPM_MAX_LOBES / 2; ++ii)
+        if (ii < hm.cnt) pv += hm.lob[ii].lam * vmf_eval(hm.lob[ii], hm.cn[ii], w[0], w[1], w[2]);
+    return pv + __shfl_xor_sync(kFull, pv, 1);
+}
+
+template <bool SAMPLE>
+__device__ __forceinline__ void epilogue_tile(const DevCfg& cfg, const float* act, int AS,
+                                              int64_t base, int64_t n, int64_t ld,
+                                              const float* __restrict__ uin, float ufrac,
+                                              float* __restrict__ dir_out,
+                                              float* __restrict__ pdf_out,
+                                              float* __restrict__ mix_out) {
+    const int t = threadIdx.x;
+    const int q = t >> 1, half = t & 1;
+    const int64_t j = base + q;
+    const bool valid = j < n;
+    const float* raw = act + q * AS;
+    HalfMix hm;
+    decode_half(cfg, raw, half, hm, mix_out, ld, j, valid);
+    float w[3];
+    bool uni = false;
+    if (SAMPLE) {
+        float u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
+        if (valid) {
+            u0 = uin[j];
+            u1 = uin[ld + j];
+            u2 = uin[2 * ld + j];
+            uni = ufrac > 0.0f && uin[3 * ld + j] < ufrac;
+        }
+        // Lobe choice: smallest i with u0 < lambda_0 + ... + lambda_i, the
+        // cumulative sum taken in lobe order: half 0 sums its lobes from 0,
+        // half 1 continues from half 0's total.
+        float run = 0.0f;
+        int sel = -1;
+        if (half == 0) {
+#pragma unroll
+            for (int ii = 0; ii < NPM_MAX_LOBES / 2; ++ii)
+                if (ii < hm.cnt) {
+                    run += hm.lob[ii].lam;
+                    if (sel < 0 && u0 < run) sel = ii;
+                }
+        }
+        const float tot0 = __shfl_xor_sync(kFull, run, 1);
+        if (half == 1) {
+            float cum = tot0;
+#pragma unroll
+            for (int ii = 0; ii < NPM_MAX_LOBES / 2; ++ii)
+                if (ii < hm.cnt) {
+                    cum += hm.lob[ii].lam;
+                    if (sel < 0 && u0 < cum) sel = ii;
+                }
+        }
+        const int osel = __shfl_xor_sync(kFull, sel, 1);
+        const int sel0 = half ? osel : sel, sel1 = half ? sel : osel;
+        const int KH = (cfg.K + 1) >> 1;
+        int owner, lidx;
+        if (sel0 >= 0) {
+            owner = 0;
+            lidx = sel0;
+        } else if (sel1 >= 0) {
+            owner = 1;
+            lidx = sel1;
+        } else {
+            const int last = cfg.K - 1;
+            owner = last >= KH ? 1 : 0;
+            lidx = last - owner * KH;
+        }
+        float d[3] = {0.0f, 0.0f, 1.0f};
+        if (half == owner) {
+            if (uni) {
+                uniform_sphere(u1, u2, d);
+            } else {
+                Lobe sl = hm.lob[0];
+#pragma unroll
+                for (int ii = 1; ii < NPM_MAX_LOBES / 2; ++ii)
+                    if (ii == lidx) sl = hm.lob[ii];
+                vmf_sample(sl, u1, u2, d);
+            }
+        }
+        const int src = (threadIdx.x & 31 & ~1) | owner;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) w[a] = __shfl_sync(kFull, d[a], src);
+    } else {
+        w[0] = w[1] = 0.0f;
+        w[2] = 1.0f;
+        if (valid) {
+            w[0] = uin[j];
+            w[1] = uin[ld + j];
+            w[2] = uin[2 * ld + j];
+        }
+    }
+    float pv = half_pdf(hm, w);
+    if (SAMPLE && ufrac > 0.0f) pv = ufrac * kInv4Pi + (1.0f - ufrac) * pv;
+    if (valid) {
+        if (half == 0) {
+            if (SAMPLE) {
+                dir_out[j] = w[0];
+                dir_out[ld + j] = w[1];
+                dir_out[2 * ld + j] = w[2];
+            }
+        } else {
+            pdf_out[j] = pv;
+        }
+    }
+}
+
+// ------------------------------------------------------ forward kernel
+
+template <bool SAMPLE>
+__global__ void __launch_bounds__(kNT) k_forward_fp32(DevCfg cfg, const float* __restrict__ grid,
+                                                      const float* __restrict__ wfwd, int64_t n,
+                                                      int64_t ld, const float* __restrict__ pos,
+                                                      const float* __restrict__ aux,
+                                                      const float* __restrict__ uin, float ufrac,
+                                                      float* __restrict__ dir_out,
+                                                      float* __restrict__ pdf_out,
+                                                      float* __restrict__ mix_out) {
+    extern __shared__ float4 smem4[];
+    float* sW = reinterpret_cast<float*>(smem4);
+    const int AS = cfg.max_width + 4;
+    float* actA = sW + cfg.fwd_floats;
+    float* actB = actA + kTQ * AS;
+    for (int i = threadIdx.x; i < cfg.fwd_floats / 4; i += kNT)
+        smem4[i] = __ldg(reinterpret_cast<const float4*>(wfwd) + i);
+    __syncthreads();
+    const int64_t ntiles = (n + kTQ - 1) / kTQ;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t base = tile * kTQ;
+        encode_tile(cfg, grid, base, n, ld, pos, aux, actA, AS);
+        __syncthreads();
+        float* in = actA;
+        float* out = actB;
+        for (int l = 0; l < cfg.n_layers; ++l) {
+            const bool last = l == cfg.n_layers - 1;
+            layer(in, AS, cfg.widths[l], sW + cfg.off_fwd[l], cfg.np_fwd[l], out, cfg.widths[l + 1],
+                  last ? 0 : 1, nullptr);
+            __syncthreads();
+            float* tmp = in;
+            in = out;
+            out = tmp;
+        }
+        epilogue_tile<SAMPLE>(cfg, in, AS, base, n, ld, uin, ufrac, dir_out, pdf_out, mix_out);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------ training kernel
+
+// Per query: raw outputs -> d(sum_j s_j log V_j)/d raw, written in place,
+// and s_j log V_j accumulated into *loss. Log-domain mixture so that log V
+// and the responsibilities r_i stay finite when V underflows FP32.
+__device__ __forceinline__ void grad_epilogue(const DevCfg& cfg, float* act, int AS, int64_t base,
+                                              int64_t n, int64_t ld,
+                                              const float* __restrict__ dir,
+                                              const float* __restrict__ rad,
+                                              const float* __restrict__ spdf,
+                                              const float* __restrict__ dlogv, float inv_n,
+                                              float* __restrict__ loss) {
+    const int t = threadIdx.x;
+    const int q = t >> 1, half = t & 1;
+    const int64_t j = base + q;
+    const bool valid = j < n;
+    float* raw = act + q * AS;
+    const int K = cfg.K, KH = (K + 1) >> 1;
+    const int l0 = half * KH, cnt = min(K, l0 + KH) - l0;
+    float w[3] = {0.0f, 0.0f, 1.0f};
+    float s = 0.0f;
+    if (valid) {
+        w[0] = dir[j];
+        w[1] = dir[ld + j];
+        w[2] = dir[2 * ld + j];
+        s = dlogv ? dlogv[j] : -(rad[j] / spdf[j]) * inv_n;
+    }
+    constexpr int H = NPM_MAX_LOBES / 2;
+    float lp[H], a[H], kap[H], md[H], wdt[H], wdp[H], sk[H], st[H], sp[H];
+    float mx = -INFINITY;
+#pragma unroll
+    for (int ii = 0; ii < H; ++ii)
+        if (ii < cnt) mx = fmaxf(mx, raw[4 * (l0 + ii)]);
+    mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, 1));
+    float ssum = 0.0f;
+#pragma unroll
+    for (int ii = 0; ii < H; ++ii)
+        if (ii < cnt) ssum += expf(raw[4 * (l0 + ii)] - mx);
+    ssum += __shfl_xor_sync(kFull, ssum, 1);
+    const float lse = mx + logf(ssum);
+    float amax = -INFINITY;
+#pragma unroll
+    for (int ii = 0; ii < H; ++ii)
+        if (ii < cnt) {
+            const int i = l0 + ii;
+            lp[ii] = raw[4 * i] - lse;  // log lambda_i
+            const float rk = raw[4 * i + 1];
+            if (cfg.kappa_act == NPM_EXP) {
+                kap[ii] = expf(rk);
+                sk[ii] = kap[ii];
+            } else {
+                kap[ii] = softplus(rk);
+                sk[ii] = logistic(rk);
+            }
+            st[ii] = logistic(raw[4 * i + 2]);
+            sp[ii] = logistic(raw[4 * i + 3]);
+            float sth, cth, sph, cph;
+            sincosf(kPi * st[ii], &sth, &cth);
+            sincosf(2.0f * kPi * sp[ii], &sph, &cph);
+            md[ii] = sth * cph * w[0] + sth * sph * w[1] + cth * w[2];
+            wdt[ii] = cth * cph * w[0] + cth * sph * w[1] - sth * w[2];
+            wdp[ii] = -sth * sph * w[0] + sth * cph * w[1];
+            a[ii] = lp[ii] + logf(vmf_scaled_norm(kap[ii])) + kap[ii] * (md[ii] - 1.0f);
+            amax = fmaxf(amax, a[ii]);
+        }
+    amax = fmaxf(amax, __shfl_xor_sync(kFull, amax, 1));
+    float es = 0.0f;
+#pragma unroll
+    for (int ii = 0; ii < H; ++ii)
+        if (ii < cnt) es += expf(a[ii] - amax);
+    es += __shfl_xor_sync(kFull, es, 1);
+    const float logV = amax + logf(es);
+#pragma unroll
+    for (int ii = 0; ii < H; ++ii)
+        if (ii < cnt) {
+            const int i = l0 + ii;
+            const float r = expf(a[ii] - logV);
+            const float lam = expf(lp[ii]);
+            const float sr = s * r;
+            raw[4 * i + 0] = s * (r - lam);
+            raw[4 * i + 1] = sr * (inv_minus_coth(kap[ii]) + md[ii]) * sk[ii];
+            raw[4 * i + 2] = sr * kap[ii] * wdt[ii] * kPi * st[ii] * (1.0f - st[ii]);
+            raw[4 * i + 3] = sr * kap[ii] * wdp[ii] * 2.0f * kPi * sp[ii] * (1.0f - sp[ii]);
+        }
+    // Zero the padding columns of the raw buffer (4K == widths[n_layers], so
+    // nothing to do) and accumulate the loss once per query.
+    float lv = (valid && half == 0) ? s * logV : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lv += __shfl_xor_sync(kFull, lv, o);
+    if ((threadIdx.x & 31) == 0 && lv != 0.0f) atomicAdd(loss, lv);
+}
+
+// dW[n][k] += sum_q dl[q][n] * h[q][k] (global atomics).
+__device__ __forceinline__ void weight_grad(const float* dl, const float* h, int AS, int N, int K,
+                                            float* __restrict__ gW) {
+    const int t = threadIdx.x;
+    const int a = t >> 4, b = t & 15;
+    for (int n0 = a * 8; n0 < N; n0 += 64)
+        for (int k0 = b * 4; k0 < K; k0 += 64) {
+            float acc[8][4];
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = 0.0f;
+            const bool two = n0 + 4 < N;
+            for (int q = 0; q < kTQ; ++q) {
+                const float4 hv = *reinterpret_cast<const float4*>(h + q * AS + k0);
+                const float4 d0 = *reinterpret_cast<const float4*>(dl + q * AS + n0);
+                float4 d1 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (two) d1 = *reinterpret_cast<const float4*>(dl + q * AS + n0 + 4);
+                const float dv[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+                const float hh[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(dv[r], hh[c], acc[r][c]);
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+                if (n0 + r < N) {
+                    float* dst = gW + (size_t)(n0 + r) * K + k0;
+                    atomicAdd(reinterpret_cast<float4*>(dst),
+                              make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]));
+                }
+        }
+}
+
+// Grid gradient: dV_l[corner] += weight * dG_l (Eq. 11 transposed).
+__device__ __forceinline__ void grid_scatter(const DevCfg& cfg, const float* denc, int AS,
+                                             int64_t base, int64_t n, int64_t ld,
+                                             const float* __restrict__ pos,
+                                             float* __restrict__ ggrid) {
+    const int t = threadIdx.x;
+    const int q = t & (kTQ - 1), part = t >> 6;
+    const int64_t j = base + q;
+    if (j >= n) return;
+    const float x = pos[j], y = pos[ld + j], z = pos[2 * ld + j];
+    const float* row = denc + q * AS;
+    const int F = cfg.feat;
+    for (int l = part; l < cfg.n_levels; l += 2) {
+        const Cell cl = make_cell(x, y, z, cfg.level_res[l]);
+        float* gl = ggrid + (size_t)cfg.level_off[l] * F;
+        const float* dg = row + l * F;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float w = corner_weight(cl, c);
+            float* e = gl + (size_t)corner_index(cfg, l, cl, c) * F;
+            if (F == 2) {
+                atomicAdd(reinterpret_cast<float2*>(e), make_float2(w * dg[0], w * dg[1]));
+            } else if (F == 4) {
+                atomicAdd(reinterpret_cast<float4*>(e),
+                          make_float4(w * dg[0], w * dg[1], w * dg[2], w * dg[3]));
+            } else {
+                for (int f = 0; f < F; ++f) atomicAdd(e + f, w * dg[f]);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kNT) k_train_fp32(DevCfg cfg, const float* __restrict__ params,
+                                                    int64_t mlp_off,
+                                                    const float* __restrict__ wfwd,
+                                                    const float* __restrict__ wbwd, int64_t n,
+                                                    int64_t ld, const float* __restrict__ pos,
+                                                    const float* __restrict__ aux,
+                                                    const float* __restrict__ dir,
+                                                    const float* __restrict__ rad,
+                                                    const float* __restrict__ spdf,
+                                                    const float* __restrict__ dlogv, float inv_n,
+                                                    float* __restrict__ grad,
+                                                    float* __restrict__ loss) {
+    extern __shared__ float4 smem4[];
+    float* sW = reinterpret_cast<float*>(smem4);
+    const int AS = cfg.max_width + 4;
+    const int L = cfg.n_layers;
+    float* buf0 = sW + cfg.fwd_floats;  // L + 2 activation buffers
+    auto buf = [&](int i) { return buf0 + i * kTQ * AS; };
+    for (int i = threadIdx.x; i < cfg.fwd_floats / 4; i += kNT)
+        smem4[i] = __ldg(reinterpret_cast<const float4*>(wfwd) + i);
+    __syncthreads();
+    const int64_t ntiles = (n + kTQ - 1) / kTQ;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t base = tile * kTQ;
+        encode_tile(cfg, params, base, n, ld, pos, aux, buf(0), AS);
+        __syncthreads();
+        for (int l = 0; l < L; ++l) {
+            layer(buf(l), AS, cfg.widths[l], sW + cfg.off_fwd[l], cfg.np_fwd[l], buf(l + 1),
+                  cfg.widths[l + 1], l == L - 1 ? 0 : 1, nullptr);
+            __syncthreads();
+        }
+        grad_epilogue(cfg, buf(L), AS, base, n, ld, dir, rad, spdf, dlogv, inv_n, loss);
+        __syncthreads();
+        // Backward: delta_L lives in buf(L); delta_{L-1} in buf(L+1);
+        // delta_{i-1} (i < L) overwrites buf(i), whose activations are spent.
+        float* dcur = buf(L);
+        for (int i = L; i >= 1; --i) {
+            const int N = cfg.widths[i], Kw = cfg.widths[i - 1];
+            float* h = buf(i - 1);
+            // Offset of W_i inside the packed MLP region.
+            int64_t woff = 0;
+            for (int m = 0; m < i - 1; ++m) woff += (int64_t)cfg.widths[m] * cfg.widths[m + 1];
+            weight_grad(dcur, h, AS, N, Kw, grad + mlp_off + woff);
+            float* dnext = (i == L) ? buf(L + 1) : buf(i);
+            layer(dcur, AS, N, wbwd + cfg.off_bwd[i - 1], cfg.np_bwd[i - 1], dnext, Kw,
+                  i > 1 ? 2 : 0, h);
+            __syncthreads();
+            dcur = dnext;
+        }
+        grid_scatter(cfg, dcur, AS, base, n, ld, pos, grad);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------- utility kernels
+
+// Arrange the MLP weights (row-major [out][in] per layer, packed) into the
+// padded forward (W^T [in][np_fwd]) and backward (W [out][np_bwd]) blobs.
+__global__ void k_arrange_weights(DevCfg cfg, const float* __restrict__ mlp,
+                                  float* __restrict__ wfwd, float* __restrict__ wbwd) {
+    int64_t woff = 0;
+    for (int l = 0; l < cfg.n_layers; ++l) {
+        const int K = cfg.widths[l], N = cfg.widths[l + 1];
+        const int npf = cfg.np_fwd[l], npb = cfg.np_bwd[l];
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K * npf; i += gridDim.x * blockDim.x) {
+            const int k = i / npf, nn = i % npf;
+            wfwd[cfg.off_fwd[l] + i] = nn < N ? mlp[woff + (int64_t)nn * K + k] : 0.0f;
+        }
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N * npb; i += gridDim.x * blockDim.x) {
+            const int nn = i / npb, k = i % npb;
+            wbwd[cfg.off_bwd[l] + i] = k < K ? mlp[woff + (int64_t)nn * K + k] : 0.0f;
+        }
+        woff += (int64_t)K * N;
+    }
+}
+
+// Dense Adam with bias correction (Kingma and Ba), c1 = 1 - b1^t,
+// c2 = 1 - b2^t. Skips the update when *loss is not finite and flags it.
+// Clears the gradient. Optionally refreshes an FP16 copy of the first
+// n_half parameters (the grid).
+__global__ void k_adam(int64_t n4, float4* __restrict__ p, float4* __restrict__ g,
+                       float4* __restrict__ m, float4* __restrict__ v, float lr, float b1, float b2,
+                       float eps, float c1, float c2, const float* __restrict__ loss,
+                       int* __restrict__ status, __half2* __restrict__ half_copy, int64_t n_half4) {
+    const bool skip = loss != nullptr && !isfinite(*loss);
+    if (skip && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatusNumeric);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float4 gg = g[i];
+        g[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (skip) continue;
+        float4 mm = m[i], vv = v[i], pp = p[i];
+        float* pm = &mm.x;
+        float* pv = &vv.x;
+        float* pg = &gg.x;
+        float* pp_ = &pp.x;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            pm[c] = b1 * pm[c] + (1.0f - b1) * pg[c];
+            pv[c] = b2 * pv[c] + (1.0f - b2) * pg[c] * pg[c];
+            const float mh = pm[c] / c1, vh = pv[c] / c2;
+            pp_[c] -= lr * mh / (sqrtf(vh) + eps);
+        }
+        m[i] = mm;
+        v[i] = vv;
+        p[i] = pp;
+        if (half_copy && i < n_half4) {
+            half_copy[2 * i] = __floats2half2_rn(pp.x, pp.y);
+            half_copy[2 * i + 1] = __floats2half2_rn(pp.z, pp.w);
+        }
+    }
+}
+
+__global__ void k_grid_indices(DevCfg cfg, int64_t n, int64_t ld, const float* __restrict__ pos,
+                               int32_t* __restrict__ out) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const float x = pos[j], y = pos[ld + j], z = pos[2 * ld + j];
+        for (int l = 0; l < cfg.n_levels; ++l) {
+            const Cell cl = make_cell(x, y, z, cfg.level_res[l]);
+            for (int c = 0; c < 8; ++c)
+                out[((int64_t)l * 8 + c) * n + j] = (int32_t)corner_index(cfg, l, cl, c);
+        }
+    }
+}
+
+__global__ void k_to_half(int64_t n, const float* __restrict__ src, __half* __restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __float2half_rn(src[i]);
+}
+
+__global__ void k_copy_loss(const float* __restrict__ acc, float* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *out = *acc;
+}
+
+// ----------------------------------------------------------- launchers
+
+size_t fwd_smem_bytes(const DevCfg& c) {
+    return sizeof(float) * ((size_t)c.fwd_floats + 2 * (size_t)kTQ * (c.max_width + 4));
+}
+
+size_t train_smem_bytes(const DevCfg& c) {
+    return sizeof(float) *
+           ((size_t)c.fwd_floats + (size_t)(c.n_layers + 2) * kTQ * (c.max_width + 4));
+}
+
+static int sm_count() {
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
+    }
+    return cached;
+}
+
+template <typename KernelT>
+static int persistent_grid(KernelT kern, size_t smem, int64_t ntiles) {
+    int per_sm = 0;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNT, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t g = (int64_t)per_sm * sm_count();
+    if (g > ntiles) g = ntiles;
+    return (int)(g < 1 ? 1 : g);
+}
+
+cudaError_t launch_forward_fp32(const DevCfg& cfg, const float* grid, const float* wfwd, int64_t n,
+                                int64_t ld, const float* pos, const float* aux, const float* uin,
+                                float ufrac, bool sample, float* dir_out, float* pdf_out,
+                                float* mix_out, cudaStream_t st) {
+    const size_t smem = fwd_smem_bytes(cfg);
+    const int64_t ntiles = (n + kTQ - 1) / kTQ;
+    if (sample) {
+        const int g = persistent_grid(k_forward_fp32<true>, smem, ntiles);
+        k_forward_fp32<true><<<g, kNT, smem, st>>>(cfg, grid, wfwd, n, ld, pos, aux, uin, ufrac,
+                                                   dir_out, pdf_out, mix_out);
+    } else {
+        const int g = persistent_grid(k_forward_fp32<false>, smem, ntiles);
+        k_forward_fp32<false><<<g, kNT, smem, st>>>(cfg, grid, wfwd, n, ld, pos, aux, uin, 0.0f,
+                                                    nullptr, pdf_out, nullptr);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_train_fp32(const DevCfg& cfg, const float* params, int64_t mlp_off,
+                              const float* wfwd, const float* wbwd, int64_t n, int64_t ld,
+                              const float* pos, const float* aux, const float* dir,
+                              const float* rad, const float* spdf, const float* dlogv,
+                              float* grad, float* loss, cudaStream_t st) {
+    const size_t smem = train_smem_bytes(cfg);
+    const int64_t ntiles = (n + kTQ - 1) / kTQ;
+    const int g = persistent_grid(k_train_fp32, smem, ntiles);
+    k_train_fp32<<<g, kNT, smem, st>>>(cfg, params, mlp_off, wfwd, wbwd, n, ld, pos, aux, dir, rad,
+                                       spdf, dlogv, 1.0f / (float)n, grad, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_arrange_weights(const DevCfg& cfg, const float* mlp, float* wfwd, float* wbwd,
+                                   cudaStream_t st) {
+    k_arrange_weights<<<32, 256, 0, st>>>(cfg, mlp, wfwd, wbwd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(int64_t n, float* p, float* g, float* m, float* v, float lr, float b1,
+                        float b2, float eps, float c1, float c2, const float* loss, int* status,
+                        __half* half_copy, int64_t n_half, cudaStream_t st) {
+    const int64_t n4 = n / 4;
+    int grid = (int)((n4 + 255) / 256);
+    const int cap = sm_count() * 8;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    k_adam<<<grid, 256, 0, st>>>(n4, reinterpret_cast<float4*>(p), reinterpret_cast<float4*>(g),
+                                 reinterpret_cast<float4*>(m), reinterpret_cast<float4*>(v), lr, b1,
+                                 b2, eps, c1, c2, loss, status,
+                                 reinterpret_cast<__half2*>(half_copy), n_half / 4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_indices(const DevCfg& cfg, int64_t n, int64_t ld, const float* pos,
+                                int32_t* out, cudaStream_t st) {
+    int grid = (int)((n + 255) / 256);
+    if (grid > 4096) grid = 4096;
+    k_grid_indices<<<grid, 256, 0, st>>>(cfg, n, ld, pos, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_half(int64_t n, const float* src, __half* dst, cudaStream_t st) {
+    int grid = (int)((n + 255) / 256);
+    if (grid > 4096) grid = 4096;
+    k_to_half<<<grid, 256, 0, st>>>(n, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_loss(const float* acc, float* out, cudaStream_t st) {
+    k_copy_loss<<<1, 32, 0, st>>>(acc, out);
+    return cudaGetLastError();
+}
+
+}  // namespace npm

@@ -1,0 +1,47 @@
+// npm_handle.h -- the library-side state behind an npm_handle (internal).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "npm.h"
+#include "npm_device.cuh"
+
+namespace npm {
+struct TcState;
+}
+
+struct npm_handle {
+    npm_config cfg;
+    npm::DevCfg dc;
+    int device = 0;
+    // Internal parameter blob: grid [0, ng), MLP weights at mlp_off (aligned
+    // to 64 floats), total n_int (a multiple of 64). The public layout packs
+    // the MLP right after the grid.
+    int64_t ng = 0, nmlp = 0, mlp_off = 0, n_int = 0;
+    float* params = nullptr;
+    float* grads = nullptr;
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    float* wfwd = nullptr;     // padded W^T blobs for the FP32 kernels
+    float* wbwd = nullptr;     // padded W blobs (backward)
+    __half* grid_h = nullptr;  // FP16 grid copy (BF16 precision)
+    float* scalars = nullptr;  // [0] loss accumulator, [8] status word
+    float* stage = nullptr;    // device staging for the _host entry points
+    cudaStream_t side[2] = {nullptr, nullptr};  // internal streams (host staging)
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    size_t fwd_smem = 0, train_smem = 0;
+    int step = 0;
+    npm::TcState* tc = nullptr;  // tensor-core (BF16) path state
+};
+
+namespace npm {
+// Tensor-core (tcgen05, BF16) path, npm_tc.cu.
+npm_status tc_create(npm_handle* h);
+void tc_destroy(npm_handle* h);
+cudaError_t tc_refresh_weights(npm_handle* h, cudaStream_t st);
+npm_status tc_query(npm_handle* h, int64_t n, int64_t ld, const float* pos, const float* aux,
+                    const float* uin, float ufrac, bool sample, float* dir_out, float* pdf_out,
+                    float* mix_out, cudaStream_t st);
+}  // namespace npm

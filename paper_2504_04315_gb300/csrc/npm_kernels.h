@@ -1,0 +1,40 @@
+// npm_kernels.h -- host-side launchers of the NPM kernels (internal).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "npm_device.cuh"
+
+namespace npm {
+
+size_t fwd_smem_bytes(const DevCfg& c);
+size_t train_smem_bytes(const DevCfg& c);
+
+cudaError_t launch_forward_fp32(const DevCfg& cfg, const float* grid, const float* wfwd, int64_t n,
+                                int64_t ld, const float* pos, const float* aux, const float* uin,
+                                float ufrac, bool sample, float* dir_out, float* pdf_out,
+                                float* mix_out, cudaStream_t st);
+
+cudaError_t launch_train_fp32(const DevCfg& cfg, const float* params, int64_t mlp_off,
+                              const float* wfwd, const float* wbwd, int64_t n, int64_t ld,
+                              const float* pos, const float* aux, const float* dir,
+                              const float* rad, const float* spdf, const float* dlogv,
+                              float* grad, float* loss, cudaStream_t st);
+
+cudaError_t launch_arrange_weights(const DevCfg& cfg, const float* mlp, float* wfwd, float* wbwd,
+                                   cudaStream_t st);
+
+cudaError_t launch_adam(int64_t n, float* p, float* g, float* m, float* v, float lr, float b1,
+                        float b2, float eps, float c1, float c2, const float* loss, int* status,
+                        __half* half_copy, int64_t n_half, cudaStream_t st);
+
+cudaError_t launch_grid_indices(const DevCfg& cfg, int64_t n, int64_t ld, const float* pos,
+                                int32_t* out, cudaStream_t st);
+
+cudaError_t launch_to_half(int64_t n, const float* src, __half* dst, cudaStream_t st);
+
+cudaError_t launch_copy_loss(const float* acc, float* out, cudaStream_t st);
+
+}  // namespace npm

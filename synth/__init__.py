@@ -190,6 +190,34 @@ def init_params(w: Workload, seed: Optional[int] = None) -> np.ndarray:
     return np.concatenate([grid] + mats).astype(np.float32)
 
 
+def random_params(w: Workload, seed: int = 1, grid_scale: float = 1.0,
+                  gain: float = 2.0, kappa_boost: float = 6.0) -> np.ndarray:
+    """Parameters that decode to varied mixtures (uneven weights, lobes spread
+    over the sphere, kappa up to tens), standing in for a trained model:
+    grid features U[-grid_scale, grid_scale], Glorot-uniform layers times
+    gain, and the kappa' rows of the last layer scaled by kappa_boost."""
+    ng = sum(grid_sizes(w)) * w.feat
+    grid = (uniform(seed, S_GRID_INIT, ng).astype(np.float64) * 2.0 - 1.0) * grid_scale
+    mats = []
+    off = 0
+    ew = encoding_width(w)
+    for i in range(len(w.widths) - 1):
+        fi, fo = w.widths[i], w.widths[i + 1]
+        # Fan-in of the first layer counts only the meaningful inputs.
+        fan_in = min(fi, ew) if i == 0 else fi
+        a = gain * math.sqrt(6.0 / (fan_in + fo))
+        u = uniform(seed, S_MLP_INIT, fi * fo, start=off).astype(np.float64)
+        off += fi * fo
+        m = ((u * 2.0 - 1.0) * a).reshape(fo, fi)
+        if i == 0 and ew < fi:
+            m[:, ew:] = 0.0
+        mats.append(m)
+    last = mats[-1]
+    for k in range(w.K):
+        last[4 * k + 1] *= kappa_boost
+    return np.concatenate([grid] + [m.ravel() for m in mats]).astype(np.float32)
+
+
 # --------------------------------------------------------------------------
 # Query inputs.
 # --------------------------------------------------------------------------
