@@ -1,35 +1,587 @@
-// npm_tc.cu -- tensor-core (tcgen05, BF16) path of the NPM forward pass.
+// npm_tc.cu -- tensor-core path of the NPM forward pass on sm_103a.
+//
+// One persistent CTA of 128 threads walks 128-query tiles; thread t owns query
+// t of the tile, which is row t of every MMA and lane t of tensor memory.
+// Per tile:
+//   encode : thread t gathers the 8 corners of every level from the FP16
+//            grid copy, blends in FP32 (Sec. 5.1, Eq. 11), appends the
+//            product-mode SH encodings (Sec. 4.3), and writes its row of the
+//            BF16 activation tile A (shared memory, UMMA K-major layout).
+//   layers : one elected thread issues tcgen05.mma kind::f16 (BF16 x BF16 ->
+//            FP32 in TMEM), M = 128, N = layer width, K in steps of 16, and
+//            commits to an mbarrier; every thread then reads its accumulator
+//            row with tcgen05.ld, applies ReLU and writes the next A row.
+//   decode : the last accumulator row (4K FP32 raw outputs) stays in
+//            registers; the thread maps it (Table 1), samples a lobe and a
+//            direction (Sec. 5.3) and evaluates the mixture (Eq. 4) in FP32.
+// Weights (BF16, pre-arranged in the UMMA layout) arrive once per CTA by a
+// bulk asynchronous copy. Every wait on an mbarrier is bounded: on timeout
+// the kernel records NPM_ERR_TIMEOUT in the status word, releases its tensor
+// memory and returns.
+#include <cuda_bf16.h>
+#include <math.h>
+
 #include "npm_handle.h"
 #include "npm_kernels.h"
 
 namespace npm {
 
-struct TcState {
-    int unused;
+namespace {
+
+constexpr int kTile = 128;
+constexpr int kThreads = 128;
+
+struct TcLayer {
+    int K, N;        // logical widths
+    int Kp, Np;      // padded to multiples of 16
+    uint32_t w_off;  // byte offset of this layer's weights in the blob
+    uint32_t idesc;  // instruction descriptor
 };
 
+struct TcCfg {
+    DevCfg base;
+    TcLayer layer[NPM_MAX_LAYERS];
+    uint32_t w_bytes;  // weight blob bytes (multiple of 16)
+    uint32_t a_bytes;  // activation tile bytes
+    uint32_t tmem_cols;
+    int enc_width;     // meaningful network inputs
+};
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor, no swizzle (core matrices of 8 rows x
+// 16 bytes): lbo = byte step between core matrices along K, sbo = byte step
+// between 8-row groups along M/N; bit 46 is the tcgen05 descriptor version.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of the barrier; false after ~2^32 cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > (1ll << 32)) return false;
+    return true;
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane. The values are
+// valid only after tmem_wait16 on the same registers.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+// tcgen05.wait::ld with the loaded registers as in/out operands, so that no
+// use of them can be scheduled before the wait.
+__device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Byte offset of element (row, k) in a K-major no-swizzle tile whose rows
+// hold kp elements: 8x8 core matrices (128 bytes), K-adjacent core matrices
+// 128 bytes apart, 8-row groups kp/8 * 128 bytes apart.
+__device__ __forceinline__ uint32_t tile_off(int row, int k, int kp) {
+    return (uint32_t)((row >> 3) * (kp >> 3) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// --------------------------------------------------------------- encode
+
+// Thread t writes row t of A (BF16, kp columns) for its query.
+__device__ __forceinline__ void tc_encode(const TcCfg& tc, const __half* __restrict__ grid_h,
+                                          int64_t j, bool valid, int64_t ld,
+                                          const float* __restrict__ pos,
+                                          const float* __restrict__ aux, uint8_t* sA, int row) {
+    const DevCfg& cfg = tc.base;
+    const int kp = tc.layer[0].Kp;
+    float x = 0.0f, y = 0.0f, z = 0.0f;
+    if (valid) {
+        x = pos[j];
+        y = pos[ld + j];
+        z = pos[2 * ld + j];
+    }
+    const int F = cfg.feat;
+    for (int l = 0; l < cfg.n_levels; ++l) {
+        const Cell cl = make_cell(x, y, z, cfg.level_res[l]);
+        const __half* gl = grid_h + (size_t)cfg.level_off[l] * F;
+        if (F == 2) {
+            float s0 = 0.0f, s1 = 0.0f;
+            uint32_t raw[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                raw[c] = __ldg(reinterpret_cast<const unsigned int*>(gl) + corner_index(cfg, l, cl, c));
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float w = corner_weight(cl, c);
+                const float2 v = __half22float2(*reinterpret_cast<const __half2*>(&raw[c]));
+                s0 = fmaf(w, v.x, s0);
+                s1 = fmaf(w, v.y, s1);
+            }
+            *reinterpret_cast<uint32_t*>(sA + tile_off(row, 2 * l, kp)) = pack_bf16(s0, s1);
+        } else {
+            float s[8];
+#pragma unroll
+            for (int f = 0; f < 8; ++f) s[f] = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float w = corner_weight(cl, c);
+                const __half* e = gl + (size_t)corner_index(cfg, l, cl, c) * F;
+#pragma unroll
+                for (int f = 0; f < 8; ++f)
+                    if (f < F) s[f] = fmaf(w, __half2float(e[f]), s[f]);
+            }
+#pragma unroll
+            for (int f = 0; f < 8; f += 2)
+                if (f < F) {
+                    const int k = l * F + f;
+                    if (f + 1 < F)
+                        *reinterpret_cast<uint32_t*>(sA + tile_off(row, k, kp)) = pack_bf16(s[f], s[f + 1]);
+                    else
+                        *reinterpret_cast<__nv_bfloat16*>(sA + tile_off(row, k, kp)) = __float2bfloat16_rn(s[f]);
+                }
+        }
+    }
+    int k = cfg.grid_feats;
+    if (cfg.mode == NPM_PRODUCT) {
+        float e[21];
+        float wo[3] = {0.0f, 0.0f, 1.0f}, nn[3] = {0.0f, 0.0f, 1.0f}, r = 0.0f;
+        if (valid) {
+            wo[0] = aux[j];
+            wo[1] = aux[ld + j];
+            wo[2] = aux[2 * ld + j];
+            nn[0] = aux[3 * ld + j];
+            nn[1] = aux[4 * ld + j];
+            nn[2] = aux[5 * ld + j];
+            r = aux[6 * ld + j];
+        }
+        sh_band4(wo[0], wo[1], wo[2], e);
+        sh_band2(nn[0], nn[1], nn[2], e + 16);
+        e[20] = r;
+#pragma unroll
+        for (int i = 0; i < 21; ++i)
+            *reinterpret_cast<__nv_bfloat16*>(sA + tile_off(row, k + i, kp)) = __float2bfloat16_rn(e[i]);
+        k += 21;
+    }
+    for (; k < kp; ++k) *reinterpret_cast<__nv_bfloat16*>(sA + tile_off(row, k, kp)) = __float2bfloat16_rn(0.0f);
+}
+
+// --------------------------------------------------------------- decode
+
+template <int KMAX>
+__device__ __forceinline__ void tc_decode(const TcCfg& tc, const float (&raw)[4 * KMAX], int64_t j,
+                                          bool valid, int64_t ld, const float* __restrict__ uin,
+                                          float ufrac, bool sample, float* __restrict__ dir_out,
+                                          float* __restrict__ pdf_out,
+                                          float* __restrict__ mix_out) {
+    const DevCfg& cfg = tc.base;
+    const int K = cfg.K;
+    Lobe lob[KMAX];
+    float cn[KMAX];
+    float mx = -INFINITY;
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i)
+        if (i < K) mx = fmaxf(mx, raw[4 * i]);
+    float ssum = 0.0f;
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i)
+        if (i < K) {
+            lob[i].lam = expf(raw[4 * i] - mx);
+            ssum += lob[i].lam;
+        }
+    const float inv = 1.0f / ssum;
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i)
+        if (i < K) {
+            lob[i].lam *= inv;
+            float th, ph;
+            decode_lobe(cfg.kappa_act, raw[4 * i + 1], raw[4 * i + 2], raw[4 * i + 3], lob[i], &th, &ph);
+            cn[i] = vmf_scaled_norm(lob[i].kap);
+            if (mix_out && valid) {
+                mix_out[(4 * i + 0) * ld + j] = lob[i].lam;
+                mix_out[(4 * i + 1) * ld + j] = lob[i].kap;
+                mix_out[(4 * i + 2) * ld + j] = th;
+                mix_out[(4 * i + 3) * ld + j] = ph;
+            }
+        }
+    float w[3] = {0.0f, 0.0f, 1.0f};
+    bool uni = false;
+    if (sample) {
+        float u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
+        if (valid) {
+            u0 = uin[j];
+            u1 = uin[ld + j];
+            u2 = uin[2 * ld + j];
+            uni = ufrac > 0.0f && uin[3 * ld + j] < ufrac;
+        }
+        if (uni) {
+            uniform_sphere(u1, u2, w);
+        } else {
+            // Smallest lobe i with u0 < lambda_0 + ... + lambda_i (last if none).
+            int sel = K - 1;
+            float cum = 0.0f;
+            bool found = false;
+#pragma unroll
+            for (int i = 0; i < KMAX; ++i)
+                if (i < K) {
+                    cum += lob[i].lam;
+                    if (!found && u0 < cum) {
+                        sel = i;
+                        found = true;
+                    }
+                }
+            Lobe sl = lob[0];
+#pragma unroll
+            for (int i = 1; i < KMAX; ++i)
+                if (i == sel) sl = lob[i];
+            vmf_sample(sl, u1, u2, w);
+        }
+    } else if (valid) {
+        w[0] = uin[j];
+        w[1] = uin[ld + j];
+        w[2] = uin[2 * ld + j];
+    }
+    float pv = 0.0f;
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i)
+        if (i < K) pv += lob[i].lam * vmf_eval(lob[i], cn[i], w[0], w[1], w[2]);
+    if (sample && ufrac > 0.0f) pv = ufrac * kInv4Pi + (1.0f - ufrac) * pv;
+    if (valid) {
+        if (sample) {
+            dir_out[j] = w[0];
+            dir_out[ld + j] = w[1];
+            dir_out[2 * ld + j] = w[2];
+        }
+        pdf_out[j] = pv;
+    }
+}
+
+// --------------------------------------------------------------- kernel
+
+template <int KMAX>
+__global__ void __launch_bounds__(kThreads) k_forward_tc(TcCfg tc, const __half* __restrict__ grid_h,
+                                                         const uint8_t* __restrict__ wblob,
+                                                         int64_t n, int64_t ld,
+                                                         const float* __restrict__ pos,
+                                                         const float* __restrict__ aux,
+                                                         const float* __restrict__ uin, float ufrac,
+                                                         int sample, float* __restrict__ dir_out,
+                                                         float* __restrict__ pdf_out,
+                                                         float* __restrict__ mix_out,
+                                                         int* __restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sW = smem;
+    uint8_t* sA = smem + tc.w_bytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sA + tc.a_bytes);  // [0] mma, [1] weights
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
+    const int t = threadIdx.x;
+    const int warp = t >> 5;
+    const uint32_t bar_mma = smem_u32(&bars[0]);
+    const uint32_t bar_w = smem_u32(&bars[1]);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(tc.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (t == 0) {
+        mbar_init(bar_mma, 1);
+        mbar_init(bar_w, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_async_smem();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    // Weights: one bulk asynchronous copy global -> shared.
+    if (t == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_w),
+                     "r"(tc.w_bytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(sW)),
+            "l"(wblob), "r"(tc.w_bytes), "r"(bar_w)
+            : "memory");
+    }
+    bool ok = !__syncthreads_or(!mbar_wait_bounded(bar_w, 0));
+    uint32_t phase = 0;
+    const uint32_t sA_addr = smem_u32(sA);
+    const uint32_t sW_addr = smem_u32(sW);
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const int L = tc.base.n_layers;
+
+    const int64_t ntiles = (n + kTile - 1) / kTile;
+    for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        const int64_t j = tile * kTile + t;
+        const bool valid = j < n;
+        tc_encode(tc, grid_h, j, valid, ld, pos, aux, sA, t);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        uint32_t raw[4 * KMAX / 16][16];
+        for (int l = 0; l < L; ++l) {
+            const TcLayer& ly = tc.layer[l];
+            if (t == 0) {
+                tc_fence_after();
+                const uint32_t sbo = (uint32_t)(ly.Kp >> 3) * 128u;
+                for (int s = 0; s < (ly.Kp >> 4); ++s) {
+                    const uint64_t ad = umma_desc(sA_addr + s * 256u, 128u, sbo);
+                    const uint64_t bd = umma_desc(sW_addr + ly.w_off + s * 256u, 128u, sbo);
+                    mma_bf16(tmem, ad, bd, ly.idesc, s > 0 ? 1u : 0u);
+                }
+                mma_commit(bar_mma);
+            }
+            const bool done = mbar_wait_bounded(bar_mma, phase);
+            phase ^= 1u;
+            ok = !__syncthreads_or(!done);
+            if (!ok) break;
+            tc_fence_after();
+            if (l < L - 1) {
+                const int kp_next = tc.layer[l + 1].Kp;
+                for (int c0 = 0; c0 < ly.Np; c0 += 16) {
+                    uint32_t r[16];
+                    tmem_ld16(tmem + lane_base + (uint32_t)c0, r);
+                    tmem_wait16(r);
+                    float v[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = fmaxf(__uint_as_float(r[i]), 0.0f);
+                    uint4 q0, q1;
+                    q0.x = pack_bf16(v[0], v[1]);
+                    q0.y = pack_bf16(v[2], v[3]);
+                    q0.z = pack_bf16(v[4], v[5]);
+                    q0.w = pack_bf16(v[6], v[7]);
+                    q1.x = pack_bf16(v[8], v[9]);
+                    q1.y = pack_bf16(v[10], v[11]);
+                    q1.z = pack_bf16(v[12], v[13]);
+                    q1.w = pack_bf16(v[14], v[15]);
+                    *reinterpret_cast<uint4*>(sA + tile_off(t, c0, kp_next)) = q0;
+                    *reinterpret_cast<uint4*>(sA + tile_off(t, c0 + 8, kp_next)) = q1;
+                }
+                fence_async_smem();
+                tc_fence_before();
+                __syncthreads();
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4 * KMAX / 16; ++c)
+                    if (c * 16 < ly.Np) tmem_ld16(tmem + lane_base + (uint32_t)(c * 16), raw[c]);
+#pragma unroll
+                for (int c = 0; c < 4 * KMAX / 16; ++c)
+                    if (c * 16 < ly.Np) tmem_wait16(raw[c]);
+                tc_fence_before();
+            }
+        }
+        if (!ok) break;
+        float rawf[4 * KMAX];
+#pragma unroll
+        for (int c = 0; c < 4 * KMAX / 16; ++c)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) rawf[c * 16 + i] = __uint_as_float(raw[c][i]);
+        tc_decode<KMAX>(tc, rawf, j, valid, ld, uin, ufrac, sample != 0, dir_out, pdf_out, mix_out);
+    }
+    if (!ok && t == 0) atomicOr(status, kStatusTimeout);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(tc.tmem_cols)
+                     : "memory");
+    }
+}
+
+// Master FP32 weights (packed [out][in] per layer) -> BF16 blob in the UMMA
+// K-major layout, zero padded to Np x Kp per layer.
+__global__ void k_tc_weights(TcCfg tc, const float* __restrict__ mlp, uint8_t* __restrict__ blob) {
+    int64_t woff = 0;
+    for (int l = 0; l < tc.base.n_layers; ++l) {
+        const TcLayer& ly = tc.layer[l];
+        const int total = ly.Np * ly.Kp;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+            const int nn = i / ly.Kp, k = i % ly.Kp;
+            const float v = (nn < ly.N && k < ly.K) ? mlp[woff + (int64_t)nn * ly.K + k] : 0.0f;
+            *reinterpret_cast<__nv_bfloat16*>(blob + ly.w_off + tile_off(nn, k, ly.Kp)) =
+                __float2bfloat16_rn(v);
+        }
+        woff += (int64_t)ly.K * ly.N;
+    }
+}
+
+}  // namespace
+
+struct TcState {
+    TcCfg cfg;
+    uint8_t* wblob = nullptr;
+    size_t smem = 0;
+    int grid = 0;
+};
+
+static int pad16(int v) { return (v + 15) / 16 * 16; }
+
 npm_status tc_create(npm_handle* h) {
-    (void)h;
-    return NPM_ERR_UNSUPPORTED;
+    const npm_config& c = h->cfg;
+    if (c.feat_per_level != 1 && c.feat_per_level != 2 && c.feat_per_level != 4 &&
+        c.feat_per_level != 8)
+        return NPM_ERR_UNSUPPORTED;
+    TcState* s = new TcState();
+    TcCfg& t = s->cfg;
+    memset(&t, 0, sizeof(t));
+    t.base = h->dc;
+    uint32_t off = 0;
+    int maxkp = 0, maxnp = 0;
+    for (int l = 0; l < c.n_layers; ++l) {
+        TcLayer& ly = t.layer[l];
+        ly.K = c.widths[l];
+        ly.N = c.widths[l + 1];
+        ly.Kp = pad16(ly.K);
+        ly.Np = pad16(ly.N);
+        ly.w_off = off;
+        off += (uint32_t)(ly.Np * ly.Kp * 2);
+        // kind::f16 descriptor: D FP32 (bit 4), A and B BF16 (bits 7, 10),
+        // both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+        ly.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ly.Np >> 3) << 17) |
+                   ((uint32_t)(kTile >> 4) << 24);
+        maxkp = ly.Kp > maxkp ? ly.Kp : maxkp;
+        maxnp = ly.Np > maxnp ? ly.Np : maxnp;
+    }
+    t.w_bytes = (off + 127u) / 128u * 128u;
+    t.a_bytes = (uint32_t)(kTile * maxkp * 2);
+    uint32_t cols = 32;
+    while ((int)cols < maxnp) cols <<= 1;
+    t.tmem_cols = cols;
+    t.enc_width = c.n_levels * c.feat_per_level + (c.mode == NPM_PRODUCT ? 21 : 0);
+    s->smem = t.w_bytes + t.a_bytes + 64;
+    if (s->smem > 200 * 1024 || c.K > 16) {
+        delete s;
+        return NPM_ERR_UNSUPPORTED;
+    }
+    if (cudaMalloc(&s->wblob, t.w_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return NPM_ERR_OOM;
+    }
+    cudaMemset(s->wblob, 0, t.w_bytes);
+    h->tc = s;
+    return NPM_OK;
 }
 
 void tc_destroy(npm_handle* h) {
+    if (!h->tc) return;
+    if (h->tc->wblob) cudaFree(h->tc->wblob);
     delete h->tc;
     h->tc = nullptr;
 }
 
 cudaError_t tc_refresh_weights(npm_handle* h, cudaStream_t st) {
-    (void)h;
-    (void)st;
-    return cudaSuccess;
+    k_tc_weights<<<16, 256, 0, st>>>(h->tc->cfg, h->params + h->mlp_off, h->tc->wblob);
+    return cudaGetLastError();
+}
+
+template <int KMAX>
+static cudaError_t launch_tc(npm_handle* h, int64_t n, int64_t ld, const float* pos,
+                             const float* aux, const float* uin, float ufrac, bool sample,
+                             float* dir_out, float* pdf_out, float* mix_out, cudaStream_t st) {
+    TcState* s = h->tc;
+    auto kern = k_forward_tc<KMAX>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, s->smem);
+    if (e != cudaSuccess) return e;
+    const int tmem_cap = (int)(512u / s->cfg.tmem_cols);
+    if (per_sm > tmem_cap) per_sm = tmem_cap;
+    if (per_sm < 1) per_sm = 1;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t ntiles = (n + kTile - 1) / kTile;
+    int64_t g = (int64_t)per_sm * sms;
+    if (g > ntiles) g = ntiles;
+    int* status = reinterpret_cast<int*>(h->scalars + 8);
+    kern<<<(int)g, kThreads, s->smem, st>>>(s->cfg, h->grid_h, s->wblob, n, ld, pos, aux, uin, ufrac,
+                                            sample ? 1 : 0, dir_out, pdf_out, mix_out, status);
+    return cudaGetLastError();
 }
 
 npm_status tc_query(npm_handle* h, int64_t n, int64_t ld, const float* pos, const float* aux,
                     const float* uin, float ufrac, bool sample, float* dir_out, float* pdf_out,
                     float* mix_out, cudaStream_t st) {
-    (void)h, (void)n, (void)ld, (void)pos, (void)aux, (void)uin, (void)ufrac, (void)sample;
-    (void)dir_out, (void)pdf_out, (void)mix_out, (void)st;
-    return NPM_ERR_UNSUPPORTED;
+    cudaError_t e;
+    const int K = h->cfg.K;
+    if (K <= 4)
+        e = launch_tc<4>(h, n, ld, pos, aux, uin, ufrac, sample, dir_out, pdf_out, mix_out, st);
+    else if (K <= 8)
+        e = launch_tc<8>(h, n, ld, pos, aux, uin, ufrac, sample, dir_out, pdf_out, mix_out, st);
+    else
+        e = launch_tc<16>(h, n, ld, pos, aux, uin, ufrac, sample, dir_out, pdf_out, mix_out, st);
+    return e == cudaSuccess ? NPM_OK : NPM_ERR_CUDA;
 }
 
 }  // namespace npm
