@@ -117,19 +117,12 @@ npm_status refresh_derived(npm_handle* h, cudaStream_t st) {
 
 }  // namespace
 
-extern "C" {
+namespace npm {
 
-const char* npm_last_error(void) { return g_last_error.c_str(); }
-
-npm_status npm_create(const npm_config* cfg, npm_handle** out) {
-    if (!out) return fail(NPM_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
+npm_status make_devcfg(const npm_config* cfg, DevCfg* out, int64_t* ng, int64_t* nmlp) {
     npm_status s = validate(cfg);
     if (s != NPM_OK) return s;
-    npm_handle* h = new npm_handle();
-    h->cfg = *cfg;
-    cudaGetDevice(&h->device);
-    npm::DevCfg& d = h->dc;
+    DevCfg& d = *out;
     memset(&d, 0, sizeof(d));
     d.mode = cfg->mode;
     d.n_levels = cfg->n_levels;
@@ -150,14 +143,12 @@ npm_status npm_create(const npm_config* cfg, npm_handle** out) {
         } else {
             off += T;
         }
-        if (off * (uint64_t)cfg->feat_per_level >= (1ull << 32)) {
-            delete h;
+        if (off * (uint64_t)cfg->feat_per_level >= (1ull << 32))
             return fail(NPM_ERR_INVALID_ARG, "grid larger than 2^32 values");
-        }
     }
-    h->ng = (int64_t)off * cfg->feat_per_level;
+    *ng = (int64_t)off * cfg->feat_per_level;
     int maxw = 0, of = 0, ob = 0;
-    h->nmlp = 0;
+    *nmlp = 0;
     for (int l = 0; l <= cfg->n_layers; ++l) {
         d.widths[l] = cfg->widths[l];
         maxw = cfg->widths[l] > maxw ? cfg->widths[l] : maxw;
@@ -170,19 +161,42 @@ npm_status npm_create(const npm_config* cfg, npm_handle** out) {
         d.off_bwd[l] = ob;
         of += K * d.np_fwd[l];
         ob += N * d.np_bwd[l];
-        h->nmlp += (int64_t)K * N;
+        *nmlp += (int64_t)K * N;
     }
     d.fwd_floats = of;
     d.bwd_floats = ob;
     d.max_width = maxw;
+    if (fwd_smem_bytes(d) > 227 * 1024)
+        return fail(NPM_ERR_UNSUPPORTED, "MLP weights do not fit in shared memory");
+    return NPM_OK;
+}
+
+npm_status set_error(npm_status s, const char* msg) { return fail(s, msg); }
+
+}  // namespace npm
+
+extern "C" {
+
+const char* npm_last_error(void) { return g_last_error.c_str(); }
+
+npm_status npm_create(const npm_config* cfg, npm_handle** out) {
+    if (!out) return fail(NPM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    npm_status s = validate(cfg);
+    if (s != NPM_OK) return s;
+    npm_handle* h = new npm_handle();
+    h->cfg = *cfg;
+    cudaGetDevice(&h->device);
+    if ((s = npm::make_devcfg(cfg, &h->dc, &h->ng, &h->nmlp)) != NPM_OK) {
+        delete h;
+        return s;
+    }
+    const npm::DevCfg& d = h->dc;
+    const int of = d.fwd_floats, ob = d.bwd_floats;
     h->mlp_off = round_up(h->ng, 64);
     h->n_int = round_up(h->mlp_off + h->nmlp, 64);
     h->fwd_smem = npm::fwd_smem_bytes(d);
     h->train_smem = npm::train_smem_bytes(d);
-    if (h->fwd_smem > 227 * 1024) {
-        delete h;
-        return fail(NPM_ERR_UNSUPPORTED, "MLP weights do not fit in shared memory");
-    }
 
     size_t nb = (size_t)(cfg->max_batch > 0 ? cfg->max_batch : 1);
     if ((s = dalloc(&h->params, h->n_int, "params")) != NPM_OK ||

@@ -37,6 +37,12 @@ struct npm_handle {
 };
 
 namespace npm {
+// Validates cfg and derives the kernels' view of it; ng / nmlp receive the
+// grid and MLP parameter counts (npm_api.cu).
+npm_status make_devcfg(const npm_config* cfg, DevCfg* out, int64_t* ng, int64_t* nmlp);
+// Records msg as the thread's last error and returns s.
+npm_status set_error(npm_status s, const char* msg);
+
 // Tensor-core (tcgen05, BF16) path, npm_tc.cu.
 npm_status tc_create(npm_handle* h);
 void tc_destroy(npm_handle* h);

@@ -1,0 +1,93 @@
+"""GPU parity of the BF16 tensor-core path (tcgen05 MLP, FP16 grid, FP32 vMF)
+against the FP64 oracle run with the FP32 master parameters.
+
+Bar: relative density error at the GPU-sampled direction, with the
+denominator floored at 1e-2/(4 pi), at most 2e-2 at the 99.9th percentile.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import PRODUCT_SMALL, cuda, host, make_model
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+PDF_P999_BF16 = 2e-2
+FLOOR = 1e-2 / (4 * math.pi)
+
+
+@pytest.fixture(autouse=True)
+def _need_cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+
+
+def _bf16_stats(w, n, seed, params=None):
+    params = synth.random_params(w, seed) if params is None else params
+    pos = synth.positions(seed, n)
+    u = synth.sample_uniforms(seed, n)
+    aux = synth.aux_inputs(seed, n) if w.mode == synth.PRODUCT else None
+    m = make_model(w, params, n, precision=synth.BF16)
+    d, p, mix = m.query_sample(cuda(pos), cuda(u), None if aux is None else cuda(aux),
+                               want_mix=True)
+    gd, gp, gm = host(d), host(p), host(mix)
+    assert np.all(np.isfinite(gp)) and np.all(gp > 0)
+    assert np.abs(np.linalg.norm(gd, axis=0) - 1).max() < 1e-5
+    ref = oracle.eval_pdf64(w, params, pos, gd.astype(np.float64), aux)
+    err = np.abs(gp - ref) / np.maximum(ref, FLOOR)
+    om = oracle.decode_batch(w, params, pos, aux)
+    m.check_device_status()
+    return err, gm, om, m, params, pos, aux
+
+
+@pytest.mark.parametrize("n", [1, 128, 1000])
+def test_tc_small_tiny(n):
+    err, gm, om, _, _, _, _ = _bf16_stats(synth.TINY_BF16, n, 21)
+    print(f"n={n} pdf err p50 {np.median(err):.2e} p99.9 {np.quantile(err, 0.999):.2e} max {err.max():.2e}")
+    assert np.quantile(err, 0.999) <= PDF_P999_BF16
+    # decoded weights match to BF16 accuracy
+    assert np.abs(gm[0::4] - om[0::4]).max() < 3e-2
+
+
+@pytest.mark.parametrize("w,n", [(synth.TINY_BF16, 1 << 16)])
+def test_tc_pdf_parity(w, n):
+    err, gm, om, _, _, _, _ = _bf16_stats(w, n, 22)
+    print(f"{w.name[:30]} n={n} pdf err p50 {np.median(err):.2e} p99.9 "
+          f"{np.quantile(err, 0.999):.2e} max {err.max():.2e}")
+    assert np.quantile(err, 0.999) <= PDF_P999_BF16
+
+
+def test_tc_eval_pdf_matches_oracle():
+    w = synth.TINY_BF16
+    n = 4096
+    params = synth.random_params(w, 23)
+    pos = synth.positions(23, n)
+    uu = synth.uniform_rows(23, synth.S_DIR, 2, n)
+    dirs = synth.sphere_dirs(uu[0], uu[1]).astype(np.float32)
+    m = make_model(w, params, n, precision=synth.BF16)
+    got = host(m.eval_pdf(cuda(pos), cuda(dirs)))
+    ref = oracle.eval_pdf(w, params, pos, dirs)
+    err = np.abs(got - ref) / np.maximum(ref, FLOOR)
+    assert np.quantile(err, 0.999) <= PDF_P999_BF16
+
+
+def test_tc_matches_fp32_path_on_lobe_choice():
+    # The BF16 path picks the same lobe as the FP32 path except near CDF
+    # boundaries: compare directions from both GPU paths.
+    w = synth.TINY_BF16
+    n = 1 << 14
+    params = synth.random_params(w, 24)
+    pos = synth.positions(24, n)
+    u = synth.sample_uniforms(24, n)
+    mb = make_model(w, params, n, precision=synth.BF16)
+    mf = make_model(w, params, n, precision=synth.FP32)
+    db, _, _ = mb.query_sample(cuda(pos), cuda(u))
+    df, _, _ = mf.query_sample(cuda(pos), cuda(u))
+    ang = np.linalg.norm(host(db) - host(df), axis=0)
+    assert np.median(ang) < 2e-2
+    assert (ang > 0.5).mean() < 2e-2
