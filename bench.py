@@ -145,11 +145,11 @@ def run_reference(args, w, rank):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(w, seconds_target=10.0):
+def cpu_baseline(w, seconds_target=12.0):
     import oracle
     oracle.build()
     params = synth.random_params(w, 3)
-    n = 2048
+    n = 4096
     pos = synth.positions(1, n)
     u = synth.sample_uniforms(1, n)
     aux = synth.aux_inputs(1, n) if w.mode == synth.PRODUCT else None
@@ -157,7 +157,7 @@ def cpu_baseline(w, seconds_target=10.0):
     oracle.query_sample(w, params, pos, u, aux)
     dt = time.perf_counter() - t0
     reps = max(1, int(seconds_target / max(dt, 1e-3)))
-    reps = min(reps, 64)
+    reps = min(reps, 20000)
     t0 = time.perf_counter()
     for _ in range(reps):
         oracle.query_sample(w, params, pos, u, aux)
@@ -170,13 +170,15 @@ def cpu_baseline(w, seconds_target=10.0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="paper_hash", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the e2e, reduced-precision and training measurements")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -241,27 +243,62 @@ def main():
 
     # End to end through the host-buffer entry point: pinned inputs copied
     # in, results copied out, inside the timed region.
-    hpos = [torch.from_numpy(synth.positions(seed0 + i, n)).pin_memory() for i in range(2)]
-    hu = [torch.from_numpy(synth.sample_uniforms(seed0 + i, n)).pin_memory() for i in range(2)]
-    haux = ([torch.from_numpy(synth.aux_inputs(seed0 + i, n)).pin_memory() for i in range(2)]
-            if w.mode == synth.PRODUCT else [None, None])
-    hd = torch.empty((3, n)).pin_memory()
-    hp = torch.empty((n,)).pin_memory()
-    for i in range(2):
-        m.query_sample_host(hpos[i], hu[i], hd, hp, haux[i], stream=stream)
-    ke = max(4, K // 4)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for i in range(ke):
-        m.query_sample_host(hpos[i % 2], hu[i % 2], hd, hp, haux[i % 2], stream=stream)
-    e2e_s = time.perf_counter() - t0
-    h2d = n * 4 * (3 + 3 + (7 if w.mode == synth.PRODUCT else 0))
-    d2h = n * 4 * 4
+    e2e = None
+    if not args.no_extras:
+        hpos = [torch.from_numpy(synth.positions(seed0 + i, n)).pin_memory() for i in range(2)]
+        hu = [torch.from_numpy(synth.sample_uniforms(seed0 + i, n)).pin_memory() for i in range(2)]
+        haux = ([torch.from_numpy(synth.aux_inputs(seed0 + i, n)).pin_memory() for i in range(2)]
+                if w.mode == synth.PRODUCT else [None, None])
+        hd = torch.empty((3, n)).pin_memory()
+        hp = torch.empty((n,)).pin_memory()
+        for i in range(2):
+            m.query_sample_host(hpos[i], hu[i], hd, hp, haux[i], stream=stream)
+        ke = max(4, K // 4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(ke):
+            m.query_sample_host(hpos[i % 2], hu[i % 2], hd, hp, haux[i % 2], stream=stream)
+        e2e_s = time.perf_counter() - t0
+        h2d = n * 4 * (3 + 3 + (7 if w.mode == synth.PRODUCT else 0))
+        d2h = n * 4 * 4
+        e2e = {"value": n * ke * world / e2e_s, "unit": "queries/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # Reduced-precision serving path: the tiny model at 2^22 queries per
+    # call in split BF16 on tensor cores, next to the FP32 CUDA-core path on
+    # the same inputs.
+    reduced = None
+    if not args.no_extras:
+        rw = synth.TINY_BF16
+        nr = rw.n_query
+        rp = synth.random_params(rw, 3)
+        rpos = torch.from_numpy(synth.positions(seed0 + 77, nr)).cuda()
+        ru = torch.from_numpy(synth.sample_uniforms(seed0 + 77, nr)).cuda()
+        rout = (torch.empty((3, nr), device="cuda"), torch.empty((nr,), device="cuda"))
+        res = {}
+        for prec in (synth.BF16X3, synth.BF16, synth.FP32):
+            mr = npm.NPM(npm.config_from(rw, max_batch=nr, precision=prec))
+            mr.set_params(rp)
+            for _ in range(3):
+                mr.query_sample(rpos, ru, out=rout, stream=stream)
+            kr = max(5, K // 4)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(kr):
+                mr.query_sample(rpos, ru, out=rout, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[prec] = nr * kr / (e0.elapsed_time(e1) / 1e3)
+            mr.close()
+        reduced = {"workload": rw.name, "queries_per_step": nr, "unit": "queries/s",
+                   "split_bf16": res[synth.BF16X3], "bf16": res[synth.BF16],
+                   "fp32_same_workload": res[synth.FP32],
+                   "split_bf16_over_fp32": res[synth.BF16X3] / res[synth.FP32]}
 
     # Training throughput (samples/s): one npm_train_step per step on the
     # product-mode workload's batch shape.
     train = None
-    if not args.no_train:
+    if not args.no_train and not args.no_extras:
         tw = synth.PRODUCT_BF16.with_(precision=synth.FP32)
         nt = tw.n_train
         mt = npm.NPM(npm.config_from(tw, max_batch=nt))
@@ -307,8 +344,7 @@ def main():
         "latency": {"p50_ms": per_sorted[len(per) // 2],
                     "p99_ms": per_sorted[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)],
                     "unit": "ms per 2^20-query batch"},
-        "e2e": {"value": n * ke * world / e2e_s, "unit": "queries/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": e2e,
         "gpu_launches": K,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved / alu_peak, "traffic": None,
@@ -316,9 +352,10 @@ def main():
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"},
         "clocks": clocks,
         "train": train,
+        "reduced_precision": reduced,
         "peaks_source": pk_src,
     }
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and not args.no_extras:
         line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)
     m.close()

@@ -62,7 +62,7 @@ typedef enum {
 
 enum { NPM_RADIANCE = 0, NPM_PRODUCT = 1 };  /* Sec. 4.1 / Sec. 4.3 */
 enum { NPM_SOFTPLUS = 0, NPM_EXP = 1 };      /* kappa mapping; Table 1 uses exp */
-enum { NPM_FP32 = 0, NPM_BF16 = 1 };         /* MLP / grid arithmetic */
+enum { NPM_FP32 = 0, NPM_BF16 = 1, NPM_BF16X3 = 2 };  /* MLP / grid arithmetic */
 
 #define NPM_MAX_LEVELS 32
 #define NPM_MAX_LAYERS 8
@@ -81,8 +81,12 @@ enum { NPM_FP32 = 0, NPM_BF16 = 1 };         /* MLP / grid arithmetic */
  *                  is a multiple of 4 and at most NPM_MAX_WIDTH.
  *   precision      NPM_FP32: FP32 grid and CUDA-core FP32 MLP.
  *                  NPM_BF16: FP16 grid copy, BF16 tensor-core MLP (tcgen05)
- *                  with FP32 accumulation; all vMF math stays FP32. Master
- *                  parameters and Adam state are FP32 in both modes.
+ *                  with FP32 accumulation; all vMF math stays FP32.
+ *                  NPM_BF16X3: as NPM_BF16, but every activation and weight
+ *                  is split into a BF16 high part and a BF16 residual, and
+ *                  each product is hi*hi + hi*lo + lo*hi (three MMAs per
+ *                  K step), which recovers about 16 significant bits.
+ *                  Master parameters and Adam state are FP32 in all modes.
  *   lr, beta1, beta2, eps   Adam (Sec. 5.3 uses lr 0.005).
  *   max_batch      largest n of any call; sizes the workspace.
  *   seed           seeds npm_create's parameter initialisation

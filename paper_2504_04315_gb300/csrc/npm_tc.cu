@@ -41,8 +41,10 @@ struct TcLayer {
 struct TcCfg {
     DevCfg base;
     TcLayer layer[NPM_MAX_LAYERS];
-    uint32_t w_bytes;  // weight blob bytes (multiple of 16)
-    uint32_t a_bytes;  // activation tile bytes
+    uint32_t w_bytes;  // bytes of one weight blob (multiple of 128); the
+                       // residual (lo) blob follows when split
+    uint32_t a_bytes;  // bytes of one activation tile; the lo tile follows
+    int split;         // 1: BF16 residual operands (three MMAs per K step)
     uint32_t tmem_cols;
     int enc_width;     // meaningful network inputs
 };
@@ -149,6 +151,43 @@ __device__ __forceinline__ uint32_t tile_off(int row, int k, int kp) {
     return (uint32_t)((row >> 3) * (kp >> 3) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
+// Rounds v to BF16 (hi) and, when lo_off != 0, also stores the BF16
+// residual v - hi at the same position of the residual tile lo_off bytes on.
+__device__ __forceinline__ void store16(uint8_t* sA, uint32_t off0, uint32_t off1, const float (&v)[16],
+                                        uint32_t lo_off) {
+    uint32_t h[8], l[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        __nv_bfloat162 hb = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        h[i] = *reinterpret_cast<uint32_t*>(&hb);
+        const float2 hf = __bfloat1622float2(hb);
+        l[i] = pack_bf16(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
+    }
+    *reinterpret_cast<uint4*>(sA + off0) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(sA + off1) = make_uint4(h[4], h[5], h[6], h[7]);
+    if (lo_off) {
+        *reinterpret_cast<uint4*>(sA + lo_off + off0) = make_uint4(l[0], l[1], l[2], l[3]);
+        *reinterpret_cast<uint4*>(sA + lo_off + off1) = make_uint4(l[4], l[5], l[6], l[7]);
+    }
+}
+
+// One or two BF16 values (and their residuals when lo_off != 0).
+__device__ __forceinline__ void store_pair(uint8_t* sA, uint32_t off, float a, float b, uint32_t lo_off) {
+    __nv_bfloat162 hb = __floats2bfloat162_rn(a, b);
+    *reinterpret_cast<__nv_bfloat162*>(sA + off) = hb;
+    if (lo_off) {
+        const float2 hf = __bfloat1622float2(hb);
+        *reinterpret_cast<uint32_t*>(sA + lo_off + off) = pack_bf16(a - hf.x, b - hf.y);
+    }
+}
+
+__device__ __forceinline__ void store_one(uint8_t* sA, uint32_t off, float a, uint32_t lo_off) {
+    const __nv_bfloat16 hb = __float2bfloat16_rn(a);
+    *reinterpret_cast<__nv_bfloat16*>(sA + off) = hb;
+    if (lo_off)
+        *reinterpret_cast<__nv_bfloat16*>(sA + lo_off + off) = __float2bfloat16_rn(a - __bfloat162float(hb));
+}
+
 // --------------------------------------------------------------- encode
 
 // Thread t writes row t of A (BF16, kp columns) for its query.
@@ -158,6 +197,7 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const __half* __restr
                                           const float* __restrict__ aux, uint8_t* sA, int row) {
     const DevCfg& cfg = tc.base;
     const int kp = tc.layer[0].Kp;
+    const uint32_t lo = tc.split ? tc.a_bytes : 0u;
     float x = 0.0f, y = 0.0f, z = 0.0f;
     if (valid) {
         x = pos[j];
@@ -181,7 +221,7 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const __half* __restr
                 s0 = fmaf(w, v.x, s0);
                 s1 = fmaf(w, v.y, s1);
             }
-            *reinterpret_cast<uint32_t*>(sA + tile_off(row, 2 * l, kp)) = pack_bf16(s0, s1);
+            store_pair(sA, tile_off(row, 2 * l, kp), s0, s1, lo);
         } else {
             float s[8];
 #pragma unroll
@@ -199,9 +239,9 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const __half* __restr
                 if (f < F) {
                     const int k = l * F + f;
                     if (f + 1 < F)
-                        *reinterpret_cast<uint32_t*>(sA + tile_off(row, k, kp)) = pack_bf16(s[f], s[f + 1]);
+                        store_pair(sA, tile_off(row, k, kp), s[f], s[f + 1], lo);
                     else
-                        *reinterpret_cast<__nv_bfloat16*>(sA + tile_off(row, k, kp)) = __float2bfloat16_rn(s[f]);
+                        store_one(sA, tile_off(row, k, kp), s[f], lo);
                 }
         }
     }
@@ -222,11 +262,10 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const __half* __restr
         sh_band2(nn[0], nn[1], nn[2], e + 16);
         e[20] = r;
 #pragma unroll
-        for (int i = 0; i < 21; ++i)
-            *reinterpret_cast<__nv_bfloat16*>(sA + tile_off(row, k + i, kp)) = __float2bfloat16_rn(e[i]);
+        for (int i = 0; i < 21; ++i) store_one(sA, tile_off(row, k + i, kp), e[i], lo);
         k += 21;
     }
-    for (; k < kp; ++k) *reinterpret_cast<__nv_bfloat16*>(sA + tile_off(row, k, kp)) = __float2bfloat16_rn(0.0f);
+    for (; k < kp; ++k) store_one(sA, tile_off(row, k, kp), 0.0f, lo);
 }
 
 // --------------------------------------------------------------- decode
@@ -333,9 +372,10 @@ __global__ void __launch_bounds__(kThreads) k_forward_tc(TcCfg tc, const __half*
                                                          float* __restrict__ mix_out,
                                                          int* __restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem[];
+    const int nsplit = tc.split ? 2 : 1;
     uint8_t* sW = smem;
-    uint8_t* sA = smem + tc.w_bytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sA + tc.a_bytes);  // [0] mma, [1] weights
+    uint8_t* sA = smem + nsplit * tc.w_bytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sA + nsplit * tc.a_bytes);  // [0] mma, [1] weights
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
     const int t = threadIdx.x;
     const int warp = t >> 5;
@@ -362,13 +402,13 @@ __global__ void __launch_bounds__(kThreads) k_forward_tc(TcCfg tc, const __half*
 
     // Weights: one bulk asynchronous copy global -> shared.
     if (t == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_w),
-                     "r"(tc.w_bytes)
+        const uint32_t wb = (uint32_t)nsplit * tc.w_bytes;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_w), "r"(wb)
                      : "memory");
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                 smem_u32(sW)),
-            "l"(wblob), "r"(tc.w_bytes), "r"(bar_w)
+            "l"(wblob), "r"(wb), "r"(bar_w)
             : "memory");
     }
     bool ok = !__syncthreads_or(!mbar_wait_bounded(bar_w, 0));
@@ -396,6 +436,13 @@ __global__ void __launch_bounds__(kThreads) k_forward_tc(TcCfg tc, const __half*
                     const uint64_t ad = umma_desc(sA_addr + s * 256u, 128u, sbo);
                     const uint64_t bd = umma_desc(sW_addr + ly.w_off + s * 256u, 128u, sbo);
                     mma_bf16(tmem, ad, bd, ly.idesc, s > 0 ? 1u : 0u);
+                    if (tc.split) {
+                        // hi*lo and lo*hi residual products
+                        const uint64_t bdl = umma_desc(sW_addr + tc.w_bytes + ly.w_off + s * 256u, 128u, sbo);
+                        const uint64_t adl = umma_desc(sA_addr + tc.a_bytes + s * 256u, 128u, sbo);
+                        mma_bf16(tmem, ad, bdl, ly.idesc, 1u);
+                        mma_bf16(tmem, adl, bd, ly.idesc, 1u);
+                    }
                 }
                 mma_commit(bar_mma);
             }
@@ -413,17 +460,8 @@ __global__ void __launch_bounds__(kThreads) k_forward_tc(TcCfg tc, const __half*
                     float v[16];
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] = fmaxf(__uint_as_float(r[i]), 0.0f);
-                    uint4 q0, q1;
-                    q0.x = pack_bf16(v[0], v[1]);
-                    q0.y = pack_bf16(v[2], v[3]);
-                    q0.z = pack_bf16(v[4], v[5]);
-                    q0.w = pack_bf16(v[6], v[7]);
-                    q1.x = pack_bf16(v[8], v[9]);
-                    q1.y = pack_bf16(v[10], v[11]);
-                    q1.z = pack_bf16(v[12], v[13]);
-                    q1.w = pack_bf16(v[14], v[15]);
-                    *reinterpret_cast<uint4*>(sA + tile_off(t, c0, kp_next)) = q0;
-                    *reinterpret_cast<uint4*>(sA + tile_off(t, c0 + 8, kp_next)) = q1;
+                    store16(sA, tile_off(t, c0, kp_next), tile_off(t, c0 + 8, kp_next), v,
+                            tc.split ? tc.a_bytes : 0u);
                 }
                 fence_async_smem();
                 tc_fence_before();
@@ -467,8 +505,11 @@ __global__ void k_tc_weights(TcCfg tc, const float* __restrict__ mlp, uint8_t* _
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
             const int nn = i / ly.Kp, k = i % ly.Kp;
             const float v = (nn < ly.N && k < ly.K) ? mlp[woff + (int64_t)nn * ly.K + k] : 0.0f;
-            *reinterpret_cast<__nv_bfloat16*>(blob + ly.w_off + tile_off(nn, k, ly.Kp)) =
-                __float2bfloat16_rn(v);
+            const __nv_bfloat16 hb = __float2bfloat16_rn(v);
+            *reinterpret_cast<__nv_bfloat16*>(blob + ly.w_off + tile_off(nn, k, ly.Kp)) = hb;
+            if (tc.split)
+                *reinterpret_cast<__nv_bfloat16*>(blob + tc.w_bytes + ly.w_off + tile_off(nn, k, ly.Kp)) =
+                    __float2bfloat16_rn(v - __bfloat162float(hb));
         }
         woff += (int64_t)ly.K * ly.N;
     }
@@ -513,21 +554,23 @@ npm_status tc_create(npm_handle* h) {
     }
     t.w_bytes = (off + 127u) / 128u * 128u;
     t.a_bytes = (uint32_t)(kTile * maxkp * 2);
+    t.split = c.precision == NPM_BF16X3 ? 1 : 0;
+    const uint32_t nsplit = t.split ? 2u : 1u;
     uint32_t cols = 32;
     while ((int)cols < maxnp) cols <<= 1;
     t.tmem_cols = cols;
     t.enc_width = c.n_levels * c.feat_per_level + (c.mode == NPM_PRODUCT ? 21 : 0);
-    s->smem = t.w_bytes + t.a_bytes + 64;
+    s->smem = nsplit * (t.w_bytes + t.a_bytes) + 64;
     if (s->smem > 200 * 1024 || c.K > 16) {
         delete s;
         return NPM_ERR_UNSUPPORTED;
     }
-    if (cudaMalloc(&s->wblob, t.w_bytes) != cudaSuccess) {
+    if (cudaMalloc(&s->wblob, nsplit * t.w_bytes) != cudaSuccess) {
         cudaGetLastError();
         delete s;
         return NPM_ERR_OOM;
     }
-    cudaMemset(s->wblob, 0, t.w_bytes);
+    cudaMemset(s->wblob, 0, nsplit * t.w_bytes);
     h->tc = s;
     return NPM_OK;
 }

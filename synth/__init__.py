@@ -83,7 +83,7 @@ RES16 = [16, 20, 25, 32, 40, 50, 64, 80, 101, 128, 161, 203, 256, 322, 406, 512]
 
 RADIANCE, PRODUCT = 0, 1
 SOFTPLUS, EXP = 0, 1
-FP32, BF16 = 0, 1
+FP32, BF16, BF16X3 = 0, 1, 2
 
 
 @dataclass
@@ -120,13 +120,13 @@ PAPER_HASH = Workload(
     widths=[32, 64, 64, 64, 32], K=8, n_query=1 << 20)
 
 TINY_BF16 = TINY.with_(
-    name="tiny dense 16^3x4, MLP 4-32-32-16, K=4, bf16 MLP / fp16 grid",
-    precision=BF16, n_query=1 << 22)
+    name="tiny dense 16^3x4, MLP 4-32-32-16, K=4, split-bf16 tensor-core MLP / fp16 grid",
+    precision=BF16X3, n_query=1 << 22)
 
 PRODUCT_BF16 = Workload(
-    name="product mode, hash grid + SH4(wo) + SH2(n) + roughness, MLP 64-64-64-64-32, K=8, bf16",
+    name="product mode, hash grid + SH4(wo) + SH2(n) + roughness, MLP 64-64-64-64-32, K=8, split-bf16",
     mode=PRODUCT, level_res=list(RES16), feat=2, log2_table=19,
-    widths=[64, 64, 64, 64, 32], K=8, precision=BF16,
+    widths=[64, 64, 64, 64, 32], K=8, precision=BF16X3,
     n_query=1 << 19, n_train=1 << 19, lr=1e-2, beta1=0.9, beta2=0.99)
 
 # Finite-difference net: 2 dense levels, hidden width 8, K=2.
