@@ -185,6 +185,50 @@ npm_status npm_backward(npm_handle* h, int64_t n, const float* pos, const float*
  * clears the gradient. */
 npm_status npm_adam_step(npm_handle* h, void* stream);
 
+/* ---------------------------------------------------- allocation-free */
+
+/* Largest padded forward-weight copy npm_eval_pdf_noalloc accepts, in
+ * floats (128 KiB of static device memory): the sum over layers of
+ * widths[l] * round_up(widths[l+1]) with round_up to 16, 32, 64 or 128. */
+#define NPM_NOALLOC_MAX_WEIGHT_FLOATS 32768
+
+/*
+ * npm_eval_pdf_noalloc -- mixture density V(dir | Theta(x)) of the FP32 path
+ * for callers that cannot allocate device memory. The paper has no
+ * counterpart; this is a deployment interface. Examples of such callers: a
+ * renderer whose device memory is owned by its own allocator or reserved up
+ * front, a plug-in that runs under a host framework that forbids
+ * cudaMalloc/cudaFree during a frame, or code that runs between other work on
+ * a stream and must not trigger the synchronisation an allocation implies.
+ *
+ * No handle is needed and nothing is allocated: the caller passes the
+ * configuration, the parameters and every input and output; the one piece of
+ * scratch the kernel needs (the padded, transposed copy of the MLP weights)
+ * lives in a file-scope device array of NPM_NOALLOC_MAX_WEIGHT_FLOATS floats
+ * that is loaded with the library on every GPU that uses it and stays
+ * resident until the process exits.
+ *   cfg      model configuration (precision is ignored: FP32 arithmetic).
+ *   params   DEVICE pointer, 16-byte aligned, npm_num_params FP32 values in
+ *            the public layout (grid, then each weight matrix row-major).
+ *   pos, aux, dir, ld, pdf_out   as for npm_eval_pdf (device pointers);
+ *            n is not limited by cfg->max_batch.
+ * Errors: NPM_ERR_INVALID_ARG (configuration or arguments),
+ * NPM_ERR_CAPACITY when the padded weights exceed
+ * NPM_NOALLOC_MAX_WEIGHT_FLOATS, NPM_ERR_CUDA on a failed launch.
+ * Set-up: the first call on each device (with that device current) looks up
+ * the device address of the scratch array once (cudaGetSymbolAddress, which
+ * also loads the library's device code if it is not loaded yet); make that
+ * first call before any stream capture.
+ * Sharing: every call on a device uses the same scratch array, which keeps
+ * the contents of the last call. Each call rewrites every value it reads, so
+ * nothing needs clearing, but calls that overlap on the GPU (different
+ * streams without ordering between them) race on the array and may read
+ * each other's weights: order them on one stream or with events.
+ */
+npm_status npm_eval_pdf_noalloc(const npm_config* cfg, const float* params, int64_t n,
+                                const float* pos, const float* aux, const float* dir, int64_t ld,
+                                float* pdf_out, void* stream);
+
 /* ------------------------------------------------------------ support */
 
 /* Number of FP32 parameters: grid (level, entry, feature), then each weight

@@ -59,6 +59,7 @@ SIGNATURES = {
     "npm_load": (st, [vp, C.c_char_p]),
     "npm_check_device_status": (st, [vp, vp]),
     "npm_last_error": (C.c_char_p, []),
+    "npm_eval_pdf_noalloc": (st, [C.POINTER(NpmConfig), vp, i64, vp, vp, vp, i64, vp, vp]),
 }
 
 _lib = None
