@@ -295,6 +295,28 @@ def main():
                    "fp32_same_workload": res[synth.FP32],
                    "split_bf16_over_fp32": res[synth.BF16X3] / res[synth.FP32]}
 
+    # Serving loop: 64 frames of 1920x1080 paths, 8 bounces with Bernoulli(0.7)
+    # survival, query + sample + pdf per bounce on the tiny network in split
+    # BF16, one training batch of 2^18 per frame; each frame is one replay of
+    # a captured CUDA graph.
+    serving = None
+    if not args.no_extras:
+        sw = synth.TINY_BF16
+        P = 1920 * 1080
+        msv = npm.NPM(npm.config_from(sw, max_batch=P))
+        msv.set_params(synth.random_params(sw, 3))
+        with npm.Wavefront(msv, P, bounces=8, survival=0.7, train_batch=1 << 18, seed=7 + rank,
+                           use_graph=True, max_frames=80) as wf:
+            wf.run(3, stream=stream)
+            sv = wf.run(64, stream=stream)
+        msv.close()
+        serving = {"workload": "1920x1080 paths x 8 bounces, survival 0.7, " + sw.name +
+                   ", 2^18 training samples per frame, CUDA-graph frames",
+                   "frames": 64, "queries": sv["queries"], "unit": "queries/s",
+                   "value": sv["queries_per_s"] * world,
+                   "bounce_p50_ms": sv["bounce_p50_ms"], "bounce_p99_ms": sv["bounce_p99_ms"],
+                   "frame_ms_mean": sv["frame_ms_mean"], "train_ms_mean": sv["train_ms_mean"]}
+
     # Training throughput (samples/s): one npm_train_step per step on the
     # product-mode workload's batch shape.
     train = None
@@ -343,7 +365,8 @@ def main():
                    "parallelism": f"dp{world} (independent batches per GPU)"},
         "latency": {"p50_ms": per_sorted[len(per) // 2],
                     "p99_ms": per_sorted[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)],
-                    "unit": "ms per 2^20-query batch"},
+                    "unit": "ms per 2^20-query batch (the serving loop's per-bounce "
+                            "latencies are under serving)"},
         "e2e": e2e,
         "gpu_launches": K,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
@@ -353,6 +376,7 @@ def main():
         "clocks": clocks,
         "train": train,
         "reduced_precision": reduced,
+        "serving": serving,
         "peaks_source": pk_src,
     }
     if not args.no_cpu_baseline and not args.no_extras:

@@ -185,6 +185,125 @@ npm_status npm_backward(npm_handle* h, int64_t n, const float* pos, const float*
  * clears the gradient. */
 npm_status npm_adam_step(npm_handle* h, void* stream);
 
+/* ------------------------------------------------------------- serving */
+
+/*
+ * Continuous-batching request loop over one handle (the batched per-bounce
+ * queries and the interleaved training batches of Sec. 5.2).
+ *
+ * Requests carry HOST arrays in the [c][ld] layout (pinned memory lets the
+ * copies overlap); they stay owned by the caller until npm_server_wait
+ * returns for the request's ticket. A worker thread admits requests in
+ * arrival order as soon as a device staging pool of pool_queries queries has
+ * room for them (admission by memory): every admitted query request of a
+ * round is served by ONE launch of the fused kernel over all of them, on one
+ * of two streams, so that requests arriving while others run join the next
+ * batch. A training request runs after every earlier query request and
+ * before every later one. Results equal those of npm_query_sample for the
+ * same inputs and parameters. While a server is attached, the handle must
+ * not be used directly. Errors: NPM_ERR_CAPACITY for n > pool_queries or
+ * n > the handle's max_batch, NPM_ERR_INVALID_ARG for bad arguments.
+ */
+typedef struct npm_server npm_server;
+
+typedef struct npm_server_stats {
+    int64_t batches;                /* kernel launches (query) and training steps */
+    int64_t requests_done;
+    int64_t queries_done;
+    int64_t train_done;
+    int64_t max_requests_per_batch; /* most requests served by one launch */
+    int64_t pool_queries;
+    int64_t pool_peak_used;
+    double latency_p50_ms;          /* submit -> results on the host */
+    double latency_p99_ms;
+} npm_server_stats;
+
+npm_status npm_server_create(npm_handle* h, int64_t pool_queries, npm_server** out);
+npm_status npm_server_submit_query(npm_server* s, int64_t n, const float* pos, const float* aux,
+                                   const float* u, int64_t ld, float uniform_frac, float* dir_out,
+                                   float* pdf_out, uint64_t* ticket);
+npm_status npm_server_submit_train(npm_server* s, int64_t n, const float* pos, const float* aux,
+                                   const float* dir, const float* radiance,
+                                   const float* sample_pdf, int64_t ld, uint64_t* ticket);
+/* Blocks until the request is complete; latency_ms (optional) receives
+ * submit-to-completion time. Each ticket can be waited for once. */
+npm_status npm_server_wait(npm_server* s, uint64_t ticket, double* latency_ms);
+npm_status npm_server_get_stats(npm_server* s, npm_server_stats* out);
+/* Completes every submitted request, then frees the server. */
+npm_status npm_server_destroy(npm_server* s);
+
+/* ------------------------------------------------- wavefront frame driver */
+
+/*
+ * A synthetic wavefront path tracer around a radiance-mode handle, standing
+ * in for the paper's renderer (Sec. 5.2): per frame, `paths` paths start at
+ * seeded positions; each of `bounces` bounces queries the guide on the
+ * compacted queue of live paths (npm_query_sample with uniform_frac),
+ * evaluates the analytic radiance of the stand-in scene times Exponential(1)
+ * noise at the sampled direction, and keeps each path with probability
+ * `survival`, moving it along the sampled direction; the first-bounce
+ * samples of the first `train_batch` paths feed one npm_train_step per frame.
+ * Queue sizes live in device memory: with use_graph the whole frame is
+ * captured once into a CUDA graph and replayed. Buffers are allocated at
+ * create; run allocates nothing. The handle must not be used by others while
+ * frames run.
+ */
+typedef struct npm_wavefront npm_wavefront;
+
+typedef struct npm_frame_config {
+    int64_t paths;        /* paths per frame (<= the handle's max_batch) */
+    int bounces;          /* bounces per frame */
+    float survival;       /* Bernoulli survival probability per bounce */
+    int64_t train_batch;  /* training samples per frame (<= paths) */
+    float uniform_frac;   /* probability of the uniform-sphere BSDF stand-in */
+    uint64_t seed;
+    int use_graph;        /* capture one frame as a CUDA graph and replay it */
+    int max_frames;       /* frames over the driver's lifetime (timestamp space) */
+} npm_frame_config;
+
+typedef struct npm_frame_stats {
+    int64_t frames;
+    int64_t queries;        /* guided queries served (sum of live paths) */
+    double seconds;         /* device time of the frames */
+    double queries_per_s;   /* queries / seconds, training included */
+    double bounce_p50_ms;   /* per-bounce batch latency on the device */
+    double bounce_p99_ms;
+    double frame_ms_mean;
+    double train_ms_mean;   /* the per-frame training step */
+    float last_loss;
+} npm_frame_stats;
+
+npm_status npm_wavefront_create(npm_handle* h, const npm_frame_config* cfg, npm_wavefront** out);
+/* Runs `frames` frames on `stream`, waits for them and fills *out. */
+npm_status npm_wavefront_run(npm_wavefront* w, int frames, void* stream, npm_frame_stats* out);
+npm_status npm_wavefront_destroy(npm_wavefront* w);
+
+/* ------------------------------------------------- synthetic stand-in scene */
+
+/*
+ * Seeded inputs and an analytic target on the device, standing in for the
+ * paper's renderer and scenes (which are not part of the method). Random
+ * numbers: SplitMix64 at counter i of (seed, stream), uniform = (bits >> 40)
+ * * 2^-24; element (r, j) of an [rows][n] block uses counter r*n + j.
+ *
+ * npm_scene_generate: positions pos [3][ld] uniform in [0,1)^3; in product
+ * mode aux [7][ld] = (wo on the normal's hemisphere, normal uniform on the
+ * sphere, roughness U[0.05, 1]); sampling uniforms u [urows][ld].
+ *
+ * npm_scene_radiance: the analytic target at (pos, dir): a sum of three vMF
+ * lobes (amplitudes 0.5/0.3/0.2, means and sharpness 1..50 varying smoothly
+ * with position; it integrates to 1 over the sphere), times in product mode
+ * max(0, n.w)(0.3 + 0.7 D(n.h)/D(1)) with a GGX D of alpha = roughness^2.
+ * clean_out [n] (optional) receives the target, noisy_out [n] (optional) the
+ * target times Exponential(1) noise drawn from (noise_seed).
+ * All pointers are device pointers; both calls are asynchronous.
+ */
+npm_status npm_scene_generate(uint64_t seed, int64_t n, int product, float* pos, float* aux,
+                              float* u, int urows, int64_t ld, void* stream);
+npm_status npm_scene_radiance(int product, uint64_t noise_seed, int64_t n, const float* pos,
+                              const float* aux, const float* dir, int64_t ld, float* clean_out,
+                              float* noisy_out, void* stream);
+
 /* ---------------------------------------------------- allocation-free */
 
 /* Largest padded forward-weight copy npm_eval_pdf_noalloc accepts, in

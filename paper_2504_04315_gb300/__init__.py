@@ -230,3 +230,110 @@ class NPM:
     def check_device_status(self, stream=None):
         _lib.check(self._L.npm_check_device_status(self._h, _stream_ptr(stream)),
                    "npm_check_device_status")
+
+
+class Server:
+    """Continuous-batching request loop over one NPM model (npm_server_* C
+    ABI). Requests carry host (CPU) tensors in the [c][ld] layout; pinned
+    memory lets the copies overlap. The model must not be used directly while
+    the server is open."""
+
+    def __init__(self, model: NPM, pool_queries: int):
+        self._L = _lib.load()
+        self.model = model
+        h = C.c_void_p()
+        _lib.check(self._L.npm_server_create(model.handle, int(pool_queries), C.byref(h)),
+                   "npm_server_create")
+        self._s = h
+        self._keep = {}
+
+    @staticmethod
+    def _host(*ts):
+        for t in ts:
+            if t is not None and (t.is_cuda or not t.is_contiguous()):
+                raise ValueError("server requests take contiguous host tensors")
+
+    def submit_query(self, pos, u, dir_out, pdf_out, aux=None, uniform_frac: float = 0.0,
+                     n: Optional[int] = None) -> int:
+        self._host(pos, u, dir_out, pdf_out, aux)
+        ld = pos.shape[1]
+        n = ld if n is None else n
+        t = C.c_uint64()
+        _lib.check(self._L.npm_server_submit_query(self._s, n, _ptr(pos), _ptr(aux), _ptr(u), ld,
+                                                   float(uniform_frac), _ptr(dir_out),
+                                                   _ptr(pdf_out), C.byref(t)),
+                   "npm_server_submit_query")
+        self._keep[t.value] = (pos, u, dir_out, pdf_out, aux)
+        return t.value
+
+    def submit_train(self, pos, dirs, radiance, sample_pdf, aux=None, n: Optional[int] = None) -> int:
+        self._host(pos, dirs, radiance, sample_pdf, aux)
+        ld = pos.shape[1]
+        n = ld if n is None else n
+        t = C.c_uint64()
+        _lib.check(self._L.npm_server_submit_train(self._s, n, _ptr(pos), _ptr(aux), _ptr(dirs),
+                                                   _ptr(radiance), _ptr(sample_pdf), ld,
+                                                   C.byref(t)), "npm_server_submit_train")
+        self._keep[t.value] = (pos, dirs, radiance, sample_pdf, aux)
+        return t.value
+
+    def wait(self, ticket: int) -> float:
+        lat = C.c_double()
+        try:
+            _lib.check(self._L.npm_server_wait(self._s, int(ticket), C.byref(lat)), "npm_server_wait")
+        finally:
+            self._keep.pop(ticket, None)
+        return lat.value
+
+    def stats(self) -> dict:
+        s = _lib.NpmServerStats()
+        _lib.check(self._L.npm_server_get_stats(self._s, C.byref(s)), "npm_server_get_stats")
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "_s", None):
+            self._L.npm_server_destroy(self._s)
+            self._s = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Wavefront:
+    """Synthetic wavefront frame driver around a radiance-mode model
+    (npm_wavefront_* C ABI)."""
+
+    def __init__(self, model: NPM, paths: int, bounces: int = 8, survival: float = 0.7,
+                 train_batch: int = 1 << 18, uniform_frac: float = 0.5, seed: int = 0,
+                 use_graph: bool = True, max_frames: int = 1024):
+        self._L = _lib.load()
+        self.model = model
+        c = _lib.NpmFrameConfig()
+        c.paths, c.bounces, c.survival = int(paths), int(bounces), float(survival)
+        c.train_batch, c.uniform_frac, c.seed = int(train_batch), float(uniform_frac), int(seed)
+        c.use_graph, c.max_frames = 1 if use_graph else 0, int(max_frames)
+        h = C.c_void_p()
+        _lib.check(self._L.npm_wavefront_create(model.handle, C.byref(c), C.byref(h)),
+                   "npm_wavefront_create")
+        self._w = h
+
+    def run(self, frames: int, stream=None) -> dict:
+        s = _lib.NpmFrameStats()
+        _lib.check(self._L.npm_wavefront_run(self._w, int(frames), _stream_ptr(stream), C.byref(s)),
+                   "npm_wavefront_run")
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "_w", None):
+            self._L.npm_wavefront_destroy(self._w)
+            self._w = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

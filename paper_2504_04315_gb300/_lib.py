@@ -31,6 +31,32 @@ class NpmConfig(C.Structure):
     ]
 
 
+class NpmServerStats(C.Structure):
+    _fields_ = [
+        ("batches", C.c_int64), ("requests_done", C.c_int64), ("queries_done", C.c_int64),
+        ("train_done", C.c_int64), ("max_requests_per_batch", C.c_int64),
+        ("pool_queries", C.c_int64), ("pool_peak_used", C.c_int64),
+        ("latency_p50_ms", C.c_double), ("latency_p99_ms", C.c_double),
+    ]
+
+
+class NpmFrameConfig(C.Structure):
+    _fields_ = [
+        ("paths", C.c_int64), ("bounces", C.c_int), ("survival", C.c_float),
+        ("train_batch", C.c_int64), ("uniform_frac", C.c_float), ("seed", C.c_uint64),
+        ("use_graph", C.c_int), ("max_frames", C.c_int),
+    ]
+
+
+class NpmFrameStats(C.Structure):
+    _fields_ = [
+        ("frames", C.c_int64), ("queries", C.c_int64), ("seconds", C.c_double),
+        ("queries_per_s", C.c_double), ("bounce_p50_ms", C.c_double),
+        ("bounce_p99_ms", C.c_double), ("frame_ms_mean", C.c_double),
+        ("train_ms_mean", C.c_double), ("last_loss", C.c_float),
+    ]
+
+
 vp = C.c_void_p
 i64 = C.c_int64
 f32 = C.c_float
@@ -59,6 +85,17 @@ SIGNATURES = {
     "npm_load": (st, [vp, C.c_char_p]),
     "npm_check_device_status": (st, [vp, vp]),
     "npm_last_error": (C.c_char_p, []),
+    "npm_wavefront_create": (st, [vp, C.POINTER(NpmFrameConfig), C.POINTER(vp)]),
+    "npm_wavefront_run": (st, [vp, C.c_int, vp, C.POINTER(NpmFrameStats)]),
+    "npm_wavefront_destroy": (st, [vp]),
+    "npm_scene_generate": (st, [C.c_uint64, i64, C.c_int, vp, vp, vp, C.c_int, i64, vp]),
+    "npm_scene_radiance": (st, [C.c_int, C.c_uint64, i64, vp, vp, vp, i64, vp, vp, vp]),
+    "npm_server_create": (st, [vp, i64, C.POINTER(vp)]),
+    "npm_server_submit_query": (st, [vp, i64, vp, vp, vp, i64, f32, vp, vp, C.POINTER(C.c_uint64)]),
+    "npm_server_submit_train": (st, [vp, i64, vp, vp, vp, vp, vp, i64, C.POINTER(C.c_uint64)]),
+    "npm_server_wait": (st, [vp, C.c_uint64, C.POINTER(C.c_double)]),
+    "npm_server_get_stats": (st, [vp, C.POINTER(NpmServerStats)]),
+    "npm_server_destroy": (st, [vp]),
     "npm_eval_pdf_noalloc": (st, [C.POINTER(NpmConfig), vp, i64, vp, vp, vp, i64, vp, vp]),
 }
 

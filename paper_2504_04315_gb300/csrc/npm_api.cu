@@ -107,6 +107,9 @@ npm_status check_call(npm_handle* h, int64_t n, int64_t ld, const void* pos, con
     return NPM_OK;
 }
 
+// Device-side count of completed Adam steps (scalars[16]).
+int* step_dev(npm_handle* h) { return reinterpret_cast<int*>(h->scalars + 16); }
+
 npm_status refresh_derived(npm_handle* h, cudaStream_t st) {
     NPM_CUDA(npm::launch_arrange_weights(h->dc, h->params + h->mlp_off, h->wfwd, h->wbwd, st),
              "arrange weights");
@@ -319,6 +322,8 @@ npm_status npm_get_grads(npm_handle* h, float* host, int64_t count) {
 
 npm_status npm_get_adam(npm_handle* h, int* step, float* m_host, float* v_host) {
     if (!h || !step) return fail(NPM_ERR_INVALID_ARG, "NULL argument");
+    NPM_CUDA(cudaDeviceSynchronize(), "synchronise");
+    NPM_CUDA(cudaMemcpy(&h->step, step_dev(h), sizeof(int), cudaMemcpyDeviceToHost), "read step");
     *step = h->step;
     npm_status s = NPM_OK;
     if (m_host && (s = copy_public(h, h->adam_m, m_host, h->ng + h->nmlp, false)) != NPM_OK) return s;
@@ -336,6 +341,7 @@ npm_status npm_set_adam(npm_handle* h, int step, const float* m_host, const floa
         (s = copy_public(h, h->adam_v, const_cast<float*>(v_host), h->ng + h->nmlp, true)) != NPM_OK)
         return s;
     h->step = step;
+    NPM_CUDA(cudaMemcpy(step_dev(h), &step, sizeof(int), cudaMemcpyHostToDevice), "write step");
     return NPM_OK;
 }
 
@@ -442,11 +448,9 @@ static npm_status backward_impl(npm_handle* h, int64_t n, const float* pos, cons
 
 static npm_status adam_impl(npm_handle* h, const float* loss, cudaStream_t st) {
     h->step += 1;
-    const double b1 = h->cfg.beta1, b2 = h->cfg.beta2;
-    const float c1 = (float)(1.0 - pow(b1, h->step)), c2 = (float)(1.0 - pow(b2, h->step));
     int* status = reinterpret_cast<int*>(h->scalars + 8);
     NPM_CUDA(npm::launch_adam(h->n_int, h->params, h->grads, h->adam_m, h->adam_v, h->cfg.lr,
-                              h->cfg.beta1, h->cfg.beta2, h->cfg.eps, c1, c2, loss, status,
+                              h->cfg.beta1, h->cfg.beta2, h->cfg.eps, step_dev(h), loss, status,
                               h->grid_h, h->grid_h ? (h->ng / 4) * 4 : 0, st),
              "adam launch");
     if (h->grid_h && h->ng % 4)
@@ -523,6 +527,8 @@ npm_status npm_save(npm_handle* h, const char* path) {
     const int64_t np = h->ng + h->nmlp;
     std::vector<float> p(np), m(np), v(np);
     npm_status s;
+    int step = 0;
+    if ((s = npm_get_adam(h, &step, nullptr, nullptr)) != NPM_OK) return s;
     if ((s = npm_get_params(h, p.data(), np)) != NPM_OK) return s;
     if ((s = copy_public(h, h->adam_m, m.data(), np, false)) != NPM_OK) return s;
     if ((s = copy_public(h, h->adam_v, v.data(), np, false)) != NPM_OK) return s;

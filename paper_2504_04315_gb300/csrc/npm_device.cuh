@@ -229,6 +229,33 @@ __device__ __forceinline__ float inv_minus_coth(float k) {
     return 1.0f / k - 1.0f - 2.0f / expm1f(2.0f * k);
 }
 
+// A batch of query requests served by one launch of a forward kernel: the
+// kernel's tiles are numbered across segments; segment s owns tiles
+// [tile0, tile0 + ceil(n / tile size)). When n_dev is set (one segment),
+// the query count is read from device memory at kernel start (graph replay
+// with device-side batch sizes).
+struct QuerySeg {
+    int64_t n, ld, tile0;
+    const float* pos;
+    const float* aux;
+    const float* uin;  // u [3 or 4][ld] when sampling, dir [3][ld] when evaluating
+    float* dir;
+    float* pdf;
+    float* mix;
+    float ufrac;
+    int pad_;
+};
+
+constexpr int kMaxSegs = 16;
+
+struct QueryBatch {
+    int nseg;
+    int sample;
+    int64_t total_tiles;
+    const int64_t* n_dev;
+    QuerySeg seg[kMaxSegs];
+};
+
 // Device status word bits (read and cleared by npm_check_device_status).
 enum : int { kStatusNumeric = 1, kStatusTimeout = 2 };
 

@@ -14,6 +14,8 @@
 // weighted log-likelihood in the log domain (Eq. 9), back-propagates through
 // the layers and scatters grid gradients with vector atomics.
 #include <math.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include "npm_device.cuh"
 #include "npm_kernels.h"
@@ -50,11 +52,10 @@ __device__ __forceinline__ void load_w(const float* p, float (&w)[NI]) {
 // padded to NP = 16 * NI columns (zeros beyond N). mode 0: identity,
 // 1: ReLU, 2: keep where mask[q][n] > 0 (ReLU derivative), else 0.
 template <int NI>
-__device__ __forceinline__ void tile_gemm(const float* __restrict__ in, int AS, int K,
+__device__ __forceinline__ void tile_gemm(int t, const float* __restrict__ in, int AS, int K,
                                           const float* __restrict__ WT, int NP,
                                           float* __restrict__ out, int N, int mode,
                                           const float* __restrict__ mask) {
-    const int t = threadIdx.x;
     const int g = t & 15, qg = t >> 4;
     float acc[8][NI];
 #pragma unroll
@@ -93,24 +94,68 @@ __device__ __forceinline__ void tile_gemm(const float* __restrict__ in, int AS, 
     }
 }
 
-__device__ __forceinline__ void layer(const float* in, int AS, int K, const float* WT, int NP,
+// One layer for the tile; only the register tiles up to NIMAX outputs per
+// thread are instantiated (NP <= 16 * NIMAX is guaranteed by the launcher).
+template <int NIMAX>
+__device__ __forceinline__ void layer(int t, const float* in, int AS, int K, const float* WT, int NP,
                                       float* out, int N, int mode, const float* mask) {
-    switch (NP) {
-        case 16: tile_gemm<1>(in, AS, K, WT, NP, out, N, mode, mask); break;
-        case 32: tile_gemm<2>(in, AS, K, WT, NP, out, N, mode, mask); break;
-        case 64: tile_gemm<4>(in, AS, K, WT, NP, out, N, mode, mask); break;
-        default: tile_gemm<8>(in, AS, K, WT, NP, out, N, mode, mask); break;
-    }
+    if (NP == 16) tile_gemm<1>(t, in, AS, K, WT, NP, out, N, mode, mask);
+    else if (NIMAX >= 2 && NP == 32) tile_gemm<(NIMAX >= 2 ? 2 : 1)>(t, in, AS, K, WT, NP, out, N, mode, mask);
+    else if (NIMAX >= 4 && NP == 64) tile_gemm<(NIMAX >= 4 ? 4 : 1)>(t, in, AS, K, WT, NP, out, N, mode, mask);
+    else if (NIMAX >= 8) tile_gemm<(NIMAX >= 8 ? 8 : 1)>(t, in, AS, K, WT, NP, out, N, mode, mask);
 }
 
 // ------------------------------------------------------------- encode
 
-// Fills act[q][0 .. widths[0]) for the tile's 64 queries.
-__device__ __forceinline__ void encode_tile(const DevCfg& cfg, const float* __restrict__ grid,
+// Blend of level l at cell cl (F features) into s[0..F).
+__device__ __forceinline__ void gather_level(const DevCfg& cfg, const float* __restrict__ grid, int l,
+                                             const Cell& cl, float (&s)[8]) {
+    const int F = cfg.feat;
+    const float* gl = grid + (size_t)cfg.level_off[l] * F;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) s[f] = 0.0f;
+    if (F == 2) {
+        float2 v[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            v[c] = __ldg(reinterpret_cast<const float2*>(gl + (size_t)corner_index(cfg, l, cl, c) * 2));
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float w = corner_weight(cl, c);
+            s[0] = fmaf(w, v[c].x, s[0]);
+            s[1] = fmaf(w, v[c].y, s[1]);
+        }
+    } else if (F == 4) {
+        float4 v[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            v[c] = __ldg(reinterpret_cast<const float4*>(gl + (size_t)corner_index(cfg, l, cl, c) * 4));
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float w = corner_weight(cl, c);
+            s[0] = fmaf(w, v[c].x, s[0]);
+            s[1] = fmaf(w, v[c].y, s[1]);
+            s[2] = fmaf(w, v[c].z, s[2]);
+            s[3] = fmaf(w, v[c].w, s[3]);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float w = corner_weight(cl, c);
+            const float* e = gl + (size_t)corner_index(cfg, l, cl, c) * F;
+#pragma unroll
+            for (int f = 0; f < 8; ++f)
+                if (f < F) s[f] = fmaf(w, __ldg(e + f), s[f]);
+        }
+    }
+}
+
+// Fills act[q][0 .. widths[0]) for the tile's 64 queries; local thread t
+// handles query t % 64 and every other level (two levels in flight).
+__device__ __forceinline__ void encode_tile(int t, const DevCfg& cfg, const float* __restrict__ grid,
                                             int64_t base, int64_t n, int64_t ld,
                                             const float* __restrict__ pos,
                                             const float* __restrict__ aux, float* act, int AS) {
-    const int t = threadIdx.x;
     const int q = t & (kTQ - 1), part = t >> 6;
     const int64_t j = base + q;
     const bool valid = j < n;
@@ -122,35 +167,27 @@ __device__ __forceinline__ void encode_tile(const DevCfg& cfg, const float* __re
     }
     float* row = act + q * AS;
     const int F = cfg.feat;
-    for (int l = part; l < cfg.n_levels; l += 2) {
-        const Cell cl = make_cell(x, y, z, cfg.level_res[l]);
-        const float* gl = grid + (size_t)cfg.level_off[l] * F;
-        float s[8];
-#pragma unroll
-        for (int f = 0; f < 8; ++f) s[f] = 0.0f;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const float w = corner_weight(cl, c);
-            const float* e = gl + (size_t)corner_index(cfg, l, cl, c) * F;
-            if (F == 2) {
-                float2 v = __ldg(reinterpret_cast<const float2*>(e));
-                s[0] += w * v.x;
-                s[1] += w * v.y;
-            } else if (F == 4) {
-                float4 v = __ldg(reinterpret_cast<const float4*>(e));
-                s[0] += w * v.x;
-                s[1] += w * v.y;
-                s[2] += w * v.z;
-                s[3] += w * v.w;
-            } else {
-#pragma unroll
-                for (int f = 0; f < 8; ++f)
-                    if (f < F) s[f] += w * __ldg(e + f);
-            }
-        }
+    int l = part;
+    for (; l + 2 < cfg.n_levels; l += 4) {
+        const Cell c0 = make_cell(x, y, z, cfg.level_res[l]);
+        const Cell c1 = make_cell(x, y, z, cfg.level_res[l + 2]);
+        float s0[8], s1[8];
+        gather_level(cfg, grid, l, c0, s0);
+        gather_level(cfg, grid, l + 2, c1, s1);
 #pragma unroll
         for (int f = 0; f < 8; ++f)
-            if (f < F) row[l * F + f] = s[f];
+            if (f < F) {
+                row[l * F + f] = s0[f];
+                row[(l + 2) * F + f] = s1[f];
+            }
+    }
+    for (; l < cfg.n_levels; l += 2) {
+        const Cell c0 = make_cell(x, y, z, cfg.level_res[l]);
+        float s0[8];
+        gather_level(cfg, grid, l, c0, s0);
+#pragma unroll
+        for (int f = 0; f < 8; ++f)
+            if (f < F) row[l * F + f] = s0[f];
     }
     const int o = cfg.grid_feats;
     const int w0 = cfg.widths[0];
@@ -190,26 +227,28 @@ __device__ __forceinline__ void encode_tile(const DevCfg& cfg, const float* __re
 
 // Mapping of one half of the lobes of query q (Table 1). Returns the local
 // lobe count; lam holds normalised weights.
+template <int KH>
 struct HalfMix {
-    Lobe lob[NPM_MAX_LOBES / 2];
-    float cn[NPM_MAX_LOBES / 2];
+    Lobe lob[KH];
+    float cn[KH];
     int l0, cnt;
 };
 
+template <int KH>
 __device__ __forceinline__ void decode_half(const DevCfg& cfg, const float* raw, int half,
-                                            HalfMix& hm, float* mix_out, int64_t ld, int64_t j,
+                                            HalfMix<KH>& hm, float* mix_out, int64_t ld, int64_t j,
                                             bool valid) {
-    const int K = cfg.K, KH = (K + 1) >> 1;
-    hm.l0 = half * KH;
-    hm.cnt = min(K, hm.l0 + KH) - hm.l0;
+    const int K = cfg.K, kh = (K + 1) >> 1;
+    hm.l0 = half * kh;
+    hm.cnt = min(K, hm.l0 + kh) - hm.l0;
     float mx = -INFINITY;
 #pragma unroll
-    for (int ii = 0; ii < NPM_MAX_LOBES / 2; ++ii)
+    for (int ii = 0; ii < KH; ++ii)
         if (ii < hm.cnt) mx = fmaxf(mx, raw[4 * (hm.l0 + ii)]);
     mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, 1));
     float ssum = 0.0f;
 #pragma unroll
-    for (int ii = 0; ii < NPM_MAX_LOBES / 2; ++ii)
+    for (int ii = 0; ii < KH; ++ii)
         if (ii < hm.cnt) {
             hm.lob[ii].lam = expf(raw[4 * (hm.l0 + ii)] - mx);
             ssum += hm.lob[ii].lam;
@@ -217,7 +256,7 @@ __device__ __forceinline__ void decode_half(const DevCfg& cfg, const float* raw,
     ssum += __shfl_xor_sync(kFull, ssum, 1);
     const float inv = 1.0f / ssum;
 #pragma unroll
-    for (int ii = 0; ii < NPM_MAX_LOBES / 2; ++ii)
+    for (int ii = 0; ii < KH; ++ii)
         if (ii < hm.cnt) {
             const int i = hm.l0 + ii;
             hm.lob[ii].lam *= inv;
@@ -234,27 +273,27 @@ __device__ __forceinline__ void decode_half(const DevCfg& cfg, const float* raw,
         }
 }
 
-__device__ __forceinline__ float half_pdf(const HalfMix& hm, const float w[3]) {
+template <int KH>
+__device__ __forceinline__ float half_pdf(const HalfMix<KH>& hm, const float w[3]) {
     float pv = 0.0f;
 #pragma unroll
-    for (int ii = 0; ii < NPM_MAX_LOBES / 2; ++ii)
+    for (int ii = 0; ii < KH; ++ii)
         if (ii < hm.cnt) pv += hm.lob[ii].lam * vmf_eval(hm.lob[ii], hm.cn[ii], w[0], w[1], w[2]);
     return pv + __shfl_xor_sync(kFull, pv, 1);
 }
 
-template <bool SAMPLE>
-__device__ __forceinline__ void epilogue_tile(const DevCfg& cfg, const float* act, int AS,
+template <bool SAMPLE, int KH>
+__device__ __forceinline__ void epilogue_tile(int t, const DevCfg& cfg, const float* act, int AS,
                                               int64_t base, int64_t n, int64_t ld,
                                               const float* __restrict__ uin, float ufrac,
                                               float* __restrict__ dir_out,
                                               float* __restrict__ pdf_out,
                                               float* __restrict__ mix_out) {
-    const int t = threadIdx.x;
     const int q = t >> 1, half = t & 1;
     const int64_t j = base + q;
     const bool valid = j < n;
     const float* raw = act + q * AS;
-    HalfMix hm;
+    HalfMix<KH> hm;
     decode_half(cfg, raw, half, hm, mix_out, ld, j, valid);
     float w[3];
     bool uni = false;
@@ -273,7 +312,7 @@ __device__ __forceinline__ void epilogue_tile(const DevCfg& cfg, const float* ac
         int sel = -1;
         if (half == 0) {
 #pragma unroll
-            for (int ii = 0; ii < NPM_MAX_LOBES / 2; ++ii)
+            for (int ii = 0; ii < KH; ++ii)
                 if (ii < hm.cnt) {
                     run += hm.lob[ii].lam;
                     if (sel < 0 && u0 < run) sel = ii;
@@ -283,7 +322,7 @@ __device__ __forceinline__ void epilogue_tile(const DevCfg& cfg, const float* ac
         if (half == 1) {
             float cum = tot0;
 #pragma unroll
-            for (int ii = 0; ii < NPM_MAX_LOBES / 2; ++ii)
+            for (int ii = 0; ii < KH; ++ii)
                 if (ii < hm.cnt) {
                     cum += hm.lob[ii].lam;
                     if (sel < 0 && u0 < cum) sel = ii;
@@ -291,7 +330,7 @@ __device__ __forceinline__ void epilogue_tile(const DevCfg& cfg, const float* ac
         }
         const int osel = __shfl_xor_sync(kFull, sel, 1);
         const int sel0 = half ? osel : sel, sel1 = half ? sel : osel;
-        const int KH = (cfg.K + 1) >> 1;
+        const int kh = (cfg.K + 1) >> 1;
         int owner, lidx;
         if (sel0 >= 0) {
             owner = 0;
@@ -301,8 +340,8 @@ __device__ __forceinline__ void epilogue_tile(const DevCfg& cfg, const float* ac
             lidx = sel1;
         } else {
             const int last = cfg.K - 1;
-            owner = last >= KH ? 1 : 0;
-            lidx = last - owner * KH;
+            owner = last >= kh ? 1 : 0;
+            lidx = last - owner * kh;
         }
         float d[3] = {0.0f, 0.0f, 1.0f};
         if (half == owner) {
@@ -311,7 +350,7 @@ __device__ __forceinline__ void epilogue_tile(const DevCfg& cfg, const float* ac
             } else {
                 Lobe sl = hm.lob[0];
 #pragma unroll
-                for (int ii = 1; ii < NPM_MAX_LOBES / 2; ++ii)
+                for (int ii = 1; ii < KH; ++ii)
                     if (ii == lidx) sl = hm.lob[ii];
                 vmf_sample(sl, u1, u2, d);
             }
@@ -345,41 +384,55 @@ __device__ __forceinline__ void epilogue_tile(const DevCfg& cfg, const float* ac
 
 // ------------------------------------------------------ forward kernel
 
-template <bool SAMPLE>
-__global__ void __launch_bounds__(kNT) k_forward_fp32(DevCfg cfg, const float* __restrict__ grid,
-                                                      const float* __restrict__ wfwd, int64_t n,
-                                                      int64_t ld, const float* __restrict__ pos,
-                                                      const float* __restrict__ aux,
-                                                      const float* __restrict__ uin, float ufrac,
-                                                      float* __restrict__ dir_out,
-                                                      float* __restrict__ pdf_out,
-                                                      float* __restrict__ mix_out) {
+__device__ __forceinline__ void group_sync(int group) {
+    asm volatile("bar.sync %0, %1;" ::"r"(group + 1), "r"(kNT) : "memory");
+}
+
+// One CTA per SM holds G tile groups of 128 threads. The groups share one
+// copy of the weights in shared memory and each walks its own 64-query tiles
+// with its own activation buffers and named barrier.
+template <bool SAMPLE, int NIMAX, int KH>
+__global__ void __launch_bounds__(512, 1) k_forward_fp32(const __grid_constant__ DevCfg cfg,
+                                                         const float* __restrict__ grid,
+                                                         const float* __restrict__ wfwd,
+                                                         const __grid_constant__ QueryBatch qb) {
     extern __shared__ float4 smem4[];
     float* sW = reinterpret_cast<float*>(smem4);
     const int AS = cfg.max_width + 4;
-    float* actA = sW + cfg.fwd_floats;
+    const int G = blockDim.x / kNT;
+    const int group = threadIdx.x / kNT;
+    const int t = threadIdx.x % kNT;
+    float* actA = sW + cfg.fwd_floats + group * 2 * kTQ * AS;
     float* actB = actA + kTQ * AS;
-    for (int i = threadIdx.x; i < cfg.fwd_floats / 4; i += kNT)
+    for (int i = threadIdx.x; i < cfg.fwd_floats / 4; i += blockDim.x)
         smem4[i] = __ldg(reinterpret_cast<const float4*>(wfwd) + i);
     __syncthreads();
-    const int64_t ntiles = (n + kTQ - 1) / kTQ;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t base = tile * kTQ;
-        encode_tile(cfg, grid, base, n, ld, pos, aux, actA, AS);
-        __syncthreads();
+    int64_t total = qb.total_tiles, n0 = qb.seg[0].n;
+    if (qb.n_dev) {
+        n0 = *qb.n_dev;
+        total = (n0 + kTQ - 1) / kTQ;
+    }
+    for (int64_t tile = (int64_t)blockIdx.x * G + group; tile < total; tile += (int64_t)gridDim.x * G) {
+        int s = 0;
+        while (s + 1 < qb.nseg && tile >= qb.seg[s + 1].tile0) ++s;
+        const QuerySeg& S = qb.seg[s];
+        const int64_t n = (s == 0 && qb.n_dev) ? n0 : S.n;
+        const int64_t base = (tile - S.tile0) * kTQ;
+        encode_tile(t, cfg, grid, base, n, S.ld, S.pos, S.aux, actA, AS);
+        group_sync(group);
         float* in = actA;
         float* out = actB;
         for (int l = 0; l < cfg.n_layers; ++l) {
             const bool last = l == cfg.n_layers - 1;
-            layer(in, AS, cfg.widths[l], sW + cfg.off_fwd[l], cfg.np_fwd[l], out, cfg.widths[l + 1],
-                  last ? 0 : 1, nullptr);
-            __syncthreads();
+            layer<NIMAX>(t, in, AS, cfg.widths[l], sW + cfg.off_fwd[l], cfg.np_fwd[l], out,
+                         cfg.widths[l + 1], last ? 0 : 1, nullptr);
+            group_sync(group);
             float* tmp = in;
             in = out;
             out = tmp;
         }
-        epilogue_tile<SAMPLE>(cfg, in, AS, base, n, ld, uin, ufrac, dir_out, pdf_out, mix_out);
-        __syncthreads();
+        epilogue_tile<SAMPLE, KH>(t, cfg, in, AS, base, n, S.ld, S.uin, S.ufrac, S.dir, S.pdf, S.mix);
+        group_sync(group);
     }
 }
 
@@ -566,11 +619,11 @@ __global__ void __launch_bounds__(kNT) k_train_fp32(DevCfg cfg, const float* __r
     const int64_t ntiles = (n + kTQ - 1) / kTQ;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t base = tile * kTQ;
-        encode_tile(cfg, params, base, n, ld, pos, aux, buf(0), AS);
+        encode_tile(threadIdx.x, cfg, params, base, n, ld, pos, aux, buf(0), AS);
         __syncthreads();
         for (int l = 0; l < L; ++l) {
-            layer(buf(l), AS, cfg.widths[l], sW + cfg.off_fwd[l], cfg.np_fwd[l], buf(l + 1),
-                  cfg.widths[l + 1], l == L - 1 ? 0 : 1, nullptr);
+            layer<8>(threadIdx.x, buf(l), AS, cfg.widths[l], sW + cfg.off_fwd[l], cfg.np_fwd[l],
+                     buf(l + 1), cfg.widths[l + 1], l == L - 1 ? 0 : 1, nullptr);
             __syncthreads();
         }
         grad_epilogue(cfg, buf(L), AS, base, n, ld, dir, rad, spdf, dlogv, inv_n, loss);
@@ -586,8 +639,8 @@ __global__ void __launch_bounds__(kNT) k_train_fp32(DevCfg cfg, const float* __r
             for (int m = 0; m < i - 1; ++m) woff += (int64_t)cfg.widths[m] * cfg.widths[m + 1];
             weight_grad(dcur, h, AS, N, Kw, grad + mlp_off + woff);
             float* dnext = (i == L) ? buf(L + 1) : buf(i);
-            layer(dcur, AS, N, wbwd + cfg.off_bwd[i - 1], cfg.np_bwd[i - 1], dnext, Kw,
-                  i > 1 ? 2 : 0, h);
+            layer<8>(threadIdx.x, dcur, AS, N, wbwd + cfg.off_bwd[i - 1], cfg.np_bwd[i - 1], dnext,
+                     Kw, i > 1 ? 2 : 0, h);
             __syncthreads();
             dcur = dnext;
         }
@@ -618,16 +671,20 @@ __global__ void k_arrange_weights(DevCfg cfg, const float* __restrict__ mlp,
     }
 }
 
-// Dense Adam with bias correction (Kingma and Ba), c1 = 1 - b1^t,
-// c2 = 1 - b2^t. Skips the update when *loss is not finite and flags it.
-// Clears the gradient. Optionally refreshes an FP16 copy of the first
-// n_half parameters (the grid).
+// Dense Adam with bias correction (Kingma and Ba) at step t = *steps + 1,
+// c1 = 1 - b1^t, c2 = 1 - b2^t; the step count lives in device memory so that
+// captured graphs replay correctly (k_step_done advances it afterwards).
+// Skips the update when *loss is not finite and flags it. Clears the
+// gradient. Optionally refreshes an FP16 copy of the first n_half parameters
+// (the grid).
 __global__ void k_adam(int64_t n4, float4* __restrict__ p, float4* __restrict__ g,
                        float4* __restrict__ m, float4* __restrict__ v, float lr, float b1, float b2,
-                       float eps, float c1, float c2, const float* __restrict__ loss,
+                       float eps, const int* __restrict__ steps, const float* __restrict__ loss,
                        int* __restrict__ status, __half2* __restrict__ half_copy, int64_t n_half4) {
     const bool skip = loss != nullptr && !isfinite(*loss);
     if (skip && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatusNumeric);
+    const float t = (float)(*steps + 1);
+    const float c1 = 1.0f - powf(b1, t), c2 = 1.0f - powf(b2, t);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
          i += (int64_t)gridDim.x * blockDim.x) {
         float4 gg = g[i];
@@ -653,6 +710,10 @@ __global__ void k_adam(int64_t n4, float4* __restrict__ p, float4* __restrict__ 
             half_copy[2 * i + 1] = __floats2half2_rn(pp.z, pp.w);
         }
     }
+}
+
+__global__ void k_step_done(int* steps) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *steps += 1;
 }
 
 __global__ void k_grid_indices(DevCfg cfg, int64_t n, int64_t ld, const float* __restrict__ pos,
@@ -710,22 +771,90 @@ static int persistent_grid(KernelT kern, size_t smem, int64_t ntiles) {
     return (int)(g < 1 ? 1 : g);
 }
 
+// Shared-memory carveout (percent of the 228 KB maximum) that holds `bytes`.
+int carveout_percent(size_t bytes) {
+    const size_t max_smem = 228 * 1024;
+    int pct = (int)((bytes * 100 + max_smem - 1) / max_smem);
+    return pct < 1 ? 1 : pct > 100 ? 100 : pct;
+}
+
+// Template instance (register tile of the widest layer, lobes per half).
+static int fp32_instance(const DevCfg& cfg) {
+    int need = 1;
+    for (int l = 0; l < cfg.n_layers; ++l) need = cfg.np_fwd[l] / 16 > need ? cfg.np_fwd[l] / 16 : need;
+    const int kh = (cfg.K + 1) / 2;
+    need = kh > need ? kh : need;
+    return need <= 2 ? 2 : need <= 4 ? 4 : 8;
+}
+
+template <bool SAMPLE, int I>
+static cudaError_t launch_fwd_inst(const DevCfg& cfg, const float* grid, const float* wfwd,
+                                   const QueryBatch& qb, int64_t tiles_hint, cudaStream_t st) {
+    auto kern = k_forward_fp32<SAMPLE, I, I>;
+    const size_t wbytes = sizeof(float) * (size_t)cfg.fwd_floats;
+    const size_t gbytes = sizeof(float) * 2 * (size_t)kTQ * (cfg.max_width + 4);
+    int G = (int)((227 * 1024 - wbytes) / gbytes);
+    if (G > 4) G = 4;
+    // Tuning override (groups per CTA) for launch-configuration sweeps.
+    if (const char* env = getenv("NPM_FP32_GROUPS")) {
+        const int g = atoi(env);
+        if (g >= 1 && g < G) G = g;
+    }
+    if (G < 1) return cudaErrorInvalidConfiguration;
+    const size_t smem = wbytes + G * gbytes;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // Carve out only the shared memory this CTA needs; the rest of the
+    // 256 KB stays L1 for the grid gathers.
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             carveout_percent(smem + 1024));
+    if (e != cudaSuccess) return e;
+    int64_t g = sm_count();
+    const int64_t need = (tiles_hint + G - 1) / G;
+    if (need < g) g = need < 1 ? 1 : need;
+    kern<<<(int)g, G * kNT, smem, st>>>(cfg, grid, wfwd, qb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward_fp32_batch(const DevCfg& cfg, const float* grid, const float* wfwd,
+                                      QueryBatch& qb, int64_t max_n, cudaStream_t st) {
+    int64_t t0 = 0;
+    for (int s = 0; s < qb.nseg; ++s) {
+        qb.seg[s].tile0 = t0;
+        t0 += (qb.seg[s].n + kTQ - 1) / kTQ;
+    }
+    qb.total_tiles = t0;
+    const int64_t hint = qb.n_dev ? (max_n + kTQ - 1) / kTQ : t0;
+    const int inst = fp32_instance(cfg);
+    if (qb.sample) {
+        if (inst == 2) return launch_fwd_inst<true, 2>(cfg, grid, wfwd, qb, hint, st);
+        if (inst == 4) return launch_fwd_inst<true, 4>(cfg, grid, wfwd, qb, hint, st);
+        return launch_fwd_inst<true, 8>(cfg, grid, wfwd, qb, hint, st);
+    }
+    if (inst == 2) return launch_fwd_inst<false, 2>(cfg, grid, wfwd, qb, hint, st);
+    if (inst == 4) return launch_fwd_inst<false, 4>(cfg, grid, wfwd, qb, hint, st);
+    return launch_fwd_inst<false, 8>(cfg, grid, wfwd, qb, hint, st);
+}
+
 cudaError_t launch_forward_fp32(const DevCfg& cfg, const float* grid, const float* wfwd, int64_t n,
                                 int64_t ld, const float* pos, const float* aux, const float* uin,
                                 float ufrac, bool sample, float* dir_out, float* pdf_out,
                                 float* mix_out, cudaStream_t st) {
-    const size_t smem = fwd_smem_bytes(cfg);
-    const int64_t ntiles = (n + kTQ - 1) / kTQ;
-    if (sample) {
-        const int g = persistent_grid(k_forward_fp32<true>, smem, ntiles);
-        k_forward_fp32<true><<<g, kNT, smem, st>>>(cfg, grid, wfwd, n, ld, pos, aux, uin, ufrac,
-                                                   dir_out, pdf_out, mix_out);
-    } else {
-        const int g = persistent_grid(k_forward_fp32<false>, smem, ntiles);
-        k_forward_fp32<false><<<g, kNT, smem, st>>>(cfg, grid, wfwd, n, ld, pos, aux, uin, 0.0f,
-                                                    nullptr, pdf_out, nullptr);
-    }
-    return cudaGetLastError();
+    QueryBatch qb;
+    memset(&qb, 0, sizeof(qb));
+    qb.nseg = 1;
+    qb.sample = sample ? 1 : 0;
+    QuerySeg& q = qb.seg[0];
+    q.n = n;
+    q.ld = ld;
+    q.pos = pos;
+    q.aux = aux;
+    q.uin = uin;
+    q.ufrac = sample ? ufrac : 0.0f;
+    q.dir = sample ? dir_out : nullptr;
+    q.pdf = pdf_out;
+    q.mix = sample ? mix_out : nullptr;
+    return launch_forward_fp32_batch(cfg, grid, wfwd, qb, n, st);
 }
 
 cudaError_t launch_train_fp32(const DevCfg& cfg, const float* params, int64_t mlp_off,
@@ -748,7 +877,7 @@ cudaError_t launch_arrange_weights(const DevCfg& cfg, const float* mlp, float* w
 }
 
 cudaError_t launch_adam(int64_t n, float* p, float* g, float* m, float* v, float lr, float b1,
-                        float b2, float eps, float c1, float c2, const float* loss, int* status,
+                        float b2, float eps, int* steps, const float* loss, int* status,
                         __half* half_copy, int64_t n_half, cudaStream_t st) {
     const int64_t n4 = n / 4;
     int grid = (int)((n4 + 255) / 256);
@@ -757,8 +886,11 @@ cudaError_t launch_adam(int64_t n, float* p, float* g, float* m, float* v, float
     if (grid < 1) grid = 1;
     k_adam<<<grid, 256, 0, st>>>(n4, reinterpret_cast<float4*>(p), reinterpret_cast<float4*>(g),
                                  reinterpret_cast<float4*>(m), reinterpret_cast<float4*>(v), lr, b1,
-                                 b2, eps, c1, c2, loss, status,
+                                 b2, eps, steps, loss, status,
                                  reinterpret_cast<__half2*>(half_copy), n_half / 4);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_step_done<<<1, 32, 0, st>>>(steps);
     return cudaGetLastError();
 }
 

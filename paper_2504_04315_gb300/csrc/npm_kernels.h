@@ -10,12 +10,19 @@
 namespace npm {
 
 size_t fwd_smem_bytes(const DevCfg& c);
+// Shared-memory carveout (percent of the maximum) that holds `bytes`.
+int carveout_percent(size_t bytes);
 size_t train_smem_bytes(const DevCfg& c);
 
 cudaError_t launch_forward_fp32(const DevCfg& cfg, const float* grid, const float* wfwd, int64_t n,
                                 int64_t ld, const float* pos, const float* aux, const float* uin,
                                 float ufrac, bool sample, float* dir_out, float* pdf_out,
                                 float* mix_out, cudaStream_t st);
+
+// Several requests in one launch (segment table; tile offsets filled in
+// here). max_n bounds the device-side count when qb.n_dev is set.
+cudaError_t launch_forward_fp32_batch(const DevCfg& cfg, const float* grid, const float* wfwd,
+                                      QueryBatch& qb, int64_t max_n, cudaStream_t st);
 
 cudaError_t launch_train_fp32(const DevCfg& cfg, const float* params, int64_t mlp_off,
                               const float* wfwd, const float* wbwd, int64_t n, int64_t ld,
@@ -26,8 +33,10 @@ cudaError_t launch_train_fp32(const DevCfg& cfg, const float* params, int64_t ml
 cudaError_t launch_arrange_weights(const DevCfg& cfg, const float* mlp, float* wfwd, float* wbwd,
                                    cudaStream_t st);
 
+// Adam at step *steps + 1 (device counter, advanced on the stream after the
+// update).
 cudaError_t launch_adam(int64_t n, float* p, float* g, float* m, float* v, float lr, float b1,
-                        float b2, float eps, float c1, float c2, const float* loss, int* status,
+                        float b2, float eps, int* steps, const float* loss, int* status,
                         __half* half_copy, int64_t n_half, cudaStream_t st);
 
 cudaError_t launch_grid_indices(const DevCfg& cfg, int64_t n, int64_t ld, const float* pos,

@@ -20,6 +20,8 @@
 // memory and returns.
 #include <cuda_bf16.h>
 #include <math.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include "npm_handle.h"
 #include "npm_kernels.h"
@@ -361,15 +363,10 @@ __device__ __forceinline__ void tc_decode(const TcCfg& tc, const float (&raw)[4 
 // --------------------------------------------------------------- kernel
 
 template <int KMAX>
-__global__ void __launch_bounds__(kThreads) k_forward_tc(TcCfg tc, const __half* __restrict__ grid_h,
+__global__ void __launch_bounds__(kThreads) k_forward_tc(const __grid_constant__ TcCfg tc,
+                                                         const __half* __restrict__ grid_h,
                                                          const uint8_t* __restrict__ wblob,
-                                                         int64_t n, int64_t ld,
-                                                         const float* __restrict__ pos,
-                                                         const float* __restrict__ aux,
-                                                         const float* __restrict__ uin, float ufrac,
-                                                         int sample, float* __restrict__ dir_out,
-                                                         float* __restrict__ pdf_out,
-                                                         float* __restrict__ mix_out,
+                                                         const __grid_constant__ QueryBatch qb,
                                                          int* __restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int nsplit = tc.split ? 2 : 1;
@@ -418,11 +415,20 @@ __global__ void __launch_bounds__(kThreads) k_forward_tc(TcCfg tc, const __half*
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     const int L = tc.base.n_layers;
 
-    const int64_t ntiles = (n + kTile - 1) / kTile;
+    int64_t ntiles = qb.total_tiles, n0 = qb.seg[0].n;
+    if (qb.n_dev) {
+        n0 = *qb.n_dev;
+        ntiles = (n0 + kTile - 1) / kTile;
+    }
     for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-        const int64_t j = tile * kTile + t;
+        int sg = 0;
+        while (sg + 1 < qb.nseg && tile >= qb.seg[sg + 1].tile0) ++sg;
+        const QuerySeg& S = qb.seg[sg];
+        const int64_t n = (sg == 0 && qb.n_dev) ? n0 : S.n;
+        const int64_t ld = S.ld;
+        const int64_t j = (tile - S.tile0) * kTile + t;
         const bool valid = j < n;
-        tc_encode(tc, grid_h, j, valid, ld, pos, aux, sA, t);
+        tc_encode(tc, grid_h, j, valid, ld, S.pos, S.aux, sA, t);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -482,7 +488,7 @@ __global__ void __launch_bounds__(kThreads) k_forward_tc(TcCfg tc, const __half*
         for (int c = 0; c < 4 * KMAX / 16; ++c)
 #pragma unroll
             for (int i = 0; i < 16; ++i) rawf[c * 16 + i] = __uint_as_float(raw[c][i]);
-        tc_decode<KMAX>(tc, rawf, j, valid, ld, uin, ufrac, sample != 0, dir_out, pdf_out, mix_out);
+        tc_decode<KMAX>(tc, rawf, j, valid, ld, S.uin, S.ufrac, qb.sample != 0, S.dir, S.pdf, S.mix);
     }
     if (!ok && t == 0) atomicOr(status, kStatusTimeout);
     tc_fence_before();
@@ -588,43 +594,71 @@ cudaError_t tc_refresh_weights(npm_handle* h, cudaStream_t st) {
 }
 
 template <int KMAX>
-static cudaError_t launch_tc(npm_handle* h, int64_t n, int64_t ld, const float* pos,
-                             const float* aux, const float* uin, float ufrac, bool sample,
-                             float* dir_out, float* pdf_out, float* mix_out, cudaStream_t st) {
+static cudaError_t launch_tc(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStream_t st) {
     TcState* s = h->tc;
     auto kern = k_forward_tc<KMAX>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, s->smem);
+    // CTAs per SM from registers and tensor memory; then carve out just the
+    // shared memory they need so the rest stays L1 for the grid gathers.
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return e;
+    const int regs_cta = ((fa.numRegs + 7) / 8 * 8) * kThreads;
+    int per_sm = regs_cta > 0 ? 65536 / regs_cta : 1;
     const int tmem_cap = (int)(512u / s->cfg.tmem_cols);
     if (per_sm > tmem_cap) per_sm = tmem_cap;
+    if (per_sm > 16) per_sm = 16;
+    while (per_sm > 1 && (size_t)per_sm * (s->smem + 1024) > 227 * 1024) --per_sm;
+    if (const char* env = getenv("NPM_TC_CTAS_PER_SM")) {
+        const int v = atoi(env);
+        if (v >= 1 && v < per_sm) per_sm = v;
+    }
     if (per_sm < 1) per_sm = 1;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             carveout_percent((size_t)per_sm * (s->smem + 1024)));
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t ntiles = (n + kTile - 1) / kTile;
+    int64_t t0 = 0;
+    for (int i = 0; i < qb.nseg; ++i) {
+        qb.seg[i].tile0 = t0;
+        t0 += (qb.seg[i].n + kTile - 1) / kTile;
+    }
+    qb.total_tiles = t0;
+    const int64_t hint = qb.n_dev ? (max_n + kTile - 1) / kTile : t0;
     int64_t g = (int64_t)per_sm * sms;
-    if (g > ntiles) g = ntiles;
+    if (g > hint) g = hint < 1 ? 1 : hint;
     int* status = reinterpret_cast<int*>(h->scalars + 8);
-    kern<<<(int)g, kThreads, s->smem, st>>>(s->cfg, h->grid_h, s->wblob, n, ld, pos, aux, uin, ufrac,
-                                            sample ? 1 : 0, dir_out, pdf_out, mix_out, status);
+    kern<<<(int)g, kThreads, s->smem, st>>>(s->cfg, h->grid_h, s->wblob, qb, status);
     return cudaGetLastError();
+}
+
+cudaError_t tc_query_batch(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStream_t st) {
+    const int K = h->cfg.K;
+    if (K <= 4) return launch_tc<4>(h, qb, max_n, st);
+    if (K <= 8) return launch_tc<8>(h, qb, max_n, st);
+    return launch_tc<16>(h, qb, max_n, st);
 }
 
 npm_status tc_query(npm_handle* h, int64_t n, int64_t ld, const float* pos, const float* aux,
                     const float* uin, float ufrac, bool sample, float* dir_out, float* pdf_out,
                     float* mix_out, cudaStream_t st) {
-    cudaError_t e;
-    const int K = h->cfg.K;
-    if (K <= 4)
-        e = launch_tc<4>(h, n, ld, pos, aux, uin, ufrac, sample, dir_out, pdf_out, mix_out, st);
-    else if (K <= 8)
-        e = launch_tc<8>(h, n, ld, pos, aux, uin, ufrac, sample, dir_out, pdf_out, mix_out, st);
-    else
-        e = launch_tc<16>(h, n, ld, pos, aux, uin, ufrac, sample, dir_out, pdf_out, mix_out, st);
-    return e == cudaSuccess ? NPM_OK : NPM_ERR_CUDA;
+    QueryBatch qb;
+    memset(&qb, 0, sizeof(qb));
+    qb.nseg = 1;
+    qb.sample = sample ? 1 : 0;
+    QuerySeg& q = qb.seg[0];
+    q.n = n;
+    q.ld = ld;
+    q.pos = pos;
+    q.aux = aux;
+    q.uin = uin;
+    q.ufrac = sample ? ufrac : 0.0f;
+    q.dir = sample ? dir_out : nullptr;
+    q.pdf = pdf_out;
+    q.mix = sample ? mix_out : nullptr;
+    return tc_query_batch(h, qb, n, st) == cudaSuccess ? NPM_OK : NPM_ERR_CUDA;
 }
 
 }  // namespace npm

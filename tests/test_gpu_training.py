@@ -1,0 +1,115 @@
+"""Training on the GPU: the device input generator matches the host one, the
+multi-step loss curve tracks the FP64 oracle, and online training (Sec. 5.2)
+gains over sampling without the guide."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import PRODUCT_SMALL, cuda, host, make_model
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(autouse=True)
+def _need_cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+
+
+@pytest.mark.parametrize("product", [False, True])
+def test_device_generator_matches_host(product):
+    from paper_2504_04315_gb300 import scene
+    n, seed = 5000, 17
+    pos, aux, u = scene.generate(seed, n, product, urows=4)
+    assert np.array_equal(host(pos), synth.positions(seed, n))
+    assert np.array_equal(host(u), synth.sample_uniforms(seed, n, rows=4))
+    ref_aux = synth.aux_inputs(seed, n) if product else None
+    if product:
+        a = host(aux)
+        # The hemisphere flip may differ only where wo is nearly tangent.
+        ok = np.abs(np.sum(ref_aux[0:3] * ref_aux[3:6], axis=0)) > 1e-4
+        assert np.abs(a[:, ok] - ref_aux[:, ok]).max() < 2e-6
+    uu = synth.uniform_rows(seed, synth.S_DIR, 2, n)
+    d = synth.sphere_dirs(uu[0], uu[1]).astype(np.float32)
+    clean, noisy = scene.radiance(product, pos, None if aux is None else cuda(ref_aux), cuda(d),
+                                  noise_seed=seed)
+    ref = synth.target(synth.positions(seed, n), d, ref_aux)
+    assert np.abs(host(clean) - ref).max() <= 2e-5 * ref.max()
+    assert np.allclose(host(noisy), ref * synth.exp_noise(seed, n), rtol=2e-5, atol=2e-5 * ref.max())
+
+
+def test_multistep_loss_curve_tracks_oracle():
+    # 30 Adam steps on fixed samples (directions uniform, so the data do not
+    # depend on the model): GPU FP32 and the FP64 oracle give the same loss
+    # at every step within 1e-3 relative.
+    w = synth.TINY
+    n = 4096
+    params = synth.random_params(w, 51)
+    b = synth.train_batch_uniform(w, n, seed=51)
+    m = make_model(w, params, n)
+    tb = [cuda(a) for a in (b.pos, b.dir, b.radiance, b.pdf)]
+    p = params.astype(np.float64)
+    mm, vv = np.zeros_like(p), np.zeros_like(p)
+    gl, ol = [], []
+    for t in range(1, 31):
+        loss = m.train_step(*tb)
+        gl.append(float(host(loss)[0]))
+        lo, g = oracle.train_grad(w, p, b.pos, b.dir, b.radiance, b.pdf)
+        ol.append(lo)
+        oracle.adam(p, g, mm, vv, t, w.lr, w.beta1, w.beta2, w.eps)
+    gl, ol = np.array(gl), np.array(ol)
+    assert ol[-1] < ol[0]
+    assert np.abs(gl - ol).max() <= 1e-3 * np.abs(ol).max(), np.abs(gl - ol).max()
+
+
+def _online(m, steps, n, seed0):
+    from paper_2504_04315_gb300 import scene
+    losses = []
+    for s in range(steps):
+        losses.append(scene.online_step(m, seed0 + s, n))
+    return [float(x) for x in torch.stack(losses).cpu().numpy().ravel()]
+
+
+def test_online_training_gains_over_uniform_radiance():
+    from paper_2504_04315_gb300 import scene
+    w = synth.TINY.with_(lr=1e-2)
+    m = make_model(w, synth.init_params(w), 1 << 16)
+    rv_untrained, _ = scene.relative_variance(m, False, 999, 1 << 16)
+    rv_uniform, mean_u = scene.relative_variance(m, False, 999, 1 << 16, uniform=True)
+    # About the paper's budget (~1000 steps); batches of 2^16.
+    losses, curve = [], []
+    for chunk in range(5):
+        losses += _online(m, 200, 1 << 16, 1000 + 200 * chunk)
+        curve.append(scene.relative_variance(m, False, 999, 1 << 16)[0])
+    rv_trained, mean_t = scene.relative_variance(m, False, 999, 1 << 16)
+    print(f"radiance: rel. variance uniform {rv_uniform:.3f} untrained {rv_untrained:.3f} "
+          f"trained every 200 steps {[round(c, 3) for c in curve]}; "
+          f"loss {losses[0]:.3f} -> {losses[-1]:.3f}")
+    assert abs(mean_u - 1.0) < 0.05 and abs(mean_t - 1.0) < 0.05  # the target integrates to 1
+    assert rv_trained < 0.5 * rv_uniform
+    assert rv_trained < 0.5 * rv_untrained
+    assert np.mean(losses[-20:]) < np.mean(losses[:20])
+
+
+def test_product_workload_200_steps():
+    # Product-mode workload: hash grid + SH(wo) + SH(n) + roughness, MLP
+    # 64-64-64-64-32, K = 8, batch 2^19, Adam lr 1e-2 / betas 0.9, 0.99,
+    # 200 online steps; split-BF16 forward for sampling.
+    from paper_2504_04315_gb300 import scene
+    w = synth.PRODUCT_BF16
+    m = make_model(w, synth.init_params(w), w.n_train)
+    rv_uniform, _ = scene.relative_variance(m, True, 4242, 1 << 16, uniform=True)
+    rv_untrained, _ = scene.relative_variance(m, True, 4242, 1 << 16)
+    losses = _online(m, 200, w.n_train, 2000)
+    rv_trained, _ = scene.relative_variance(m, True, 4242, 1 << 16)
+    m.check_device_status()
+    print(f"product: rel. variance uniform {rv_uniform:.3f} untrained {rv_untrained:.3f} "
+          f"trained {rv_trained:.3f}; loss {losses[0]:.3f} -> {losses[-1]:.3f}")
+    assert all(math.isfinite(x) for x in losses)
+    assert np.mean(losses[-20:]) < np.mean(losses[:20])
+    assert rv_trained < 0.5 * rv_uniform
