@@ -225,6 +225,10 @@ npm_status npm_server_submit_query(npm_server* s, int64_t n, const float* pos, c
 npm_status npm_server_submit_train(npm_server* s, int64_t n, const float* pos, const float* aux,
                                    const float* dir, const float* radiance,
                                    const float* sample_pdf, int64_t ld, uint64_t* ticket);
+/* hold != 0 pauses admission (submitted requests queue up); hold == 0
+ * resumes it, and everything queued is admitted together as memory allows.
+ * npm_server_destroy releases a hold. */
+npm_status npm_server_hold(npm_server* s, int hold);
 /* Blocks until the request is complete; latency_ms (optional) receives
  * submit-to-completion time. Each ticket can be waited for once. */
 npm_status npm_server_wait(npm_server* s, uint64_t ticket, double* latency_ms);

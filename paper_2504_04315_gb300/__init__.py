@@ -277,6 +277,11 @@ class Server:
         self._keep[t.value] = (pos, dirs, radiance, sample_pdf, aux)
         return t.value
 
+    def hold(self, on: bool = True):
+        """Pause (True) or resume (False) admission; requests submitted while
+        held are admitted together on resume."""
+        _lib.check(self._L.npm_server_hold(self._s, 1 if on else 0), "npm_server_hold")
+
     def wait(self, ticket: int) -> float:
         lat = C.c_double()
         try:

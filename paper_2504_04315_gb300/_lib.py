@@ -93,6 +93,7 @@ SIGNATURES = {
     "npm_server_create": (st, [vp, i64, C.POINTER(vp)]),
     "npm_server_submit_query": (st, [vp, i64, vp, vp, vp, i64, f32, vp, vp, C.POINTER(C.c_uint64)]),
     "npm_server_submit_train": (st, [vp, i64, vp, vp, vp, vp, vp, i64, C.POINTER(C.c_uint64)]),
+    "npm_server_hold": (st, [vp, C.c_int]),
     "npm_server_wait": (st, [vp, C.c_uint64, C.POINTER(C.c_double)]),
     "npm_server_get_stats": (st, [vp, C.POINTER(NpmServerStats)]),
     "npm_server_destroy": (st, [vp]),

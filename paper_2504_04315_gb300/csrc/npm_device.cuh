@@ -157,6 +157,41 @@ __device__ __forceinline__ void decode_lobe(int kappa_act, float rk, float rt, f
     if (phi) *phi = ph;
 }
 
+// Forward-path variant of decode_lobe on the hardware approximations
+// (__expf, __logf, __sincosf, __fdividef). Arguments stay where those are
+// accurate: sine/cosine arguments in [-pi, pi] (absolute error < 4e-7);
+// exponentials of arguments |x| <~ 100 (relative error ~|x| 2^-24).
+// phi = 2 pi s(phi') is evaluated as pi + pi (2 s - 1), so that
+// (sin, cos)(phi) = -(sin, cos)(pi (2 s - 1)).
+__device__ __forceinline__ float logistic_fast(float t) {
+    return __fdividef(1.0f, 1.0f + __expf(-t));
+}
+
+__device__ __forceinline__ float softplus_fast(float t) {
+    // max(t, 0) + log1p(e^{-|t|}); the log of 1 + e loses only absolute
+    // accuracy (~6e-8), which kappa tolerates at every scale.
+    return fmaxf(t, 0.0f) + __logf(1.0f + __expf(-fabsf(t)));
+}
+
+__device__ __forceinline__ void decode_lobe_fast(int kappa_act, float rk, float rt, float rp, Lobe& L,
+                                                 float* theta, float* phi) {
+    L.kap = kappa_act == NPM_EXP ? __expf(rk) : softplus_fast(rk);
+    const float st = logistic_fast(rt), sp = logistic_fast(rp);
+    const float th = kPi * st;
+    const float ph_c = kPi * (2.0f * sp - 1.0f);  // phi - pi, in [-pi, pi]
+    float sth, cth, sph, cph;
+    __sincosf(th - 0.5f * kPi, &cth, &sth);       // sin(th) = cos(th - pi/2), cos(th) = -sin(th - pi/2)
+    cth = -cth;
+    __sincosf(ph_c, &sph, &cph);
+    sph = -sph;
+    cph = -cph;
+    L.mu[0] = sth * cph;
+    L.mu[1] = sth * sph;
+    L.mu[2] = cth;
+    if (theta) *theta = th;
+    if (phi) *phi = ph_c + kPi;
+}
+
 // ------------------------------------------------------ vMF (Eq. 3-4)
 
 // kappa / (4 pi sinh kappa) * e^kappa, written kappa / (2 pi (1 - e^{-2 kappa}))
@@ -169,6 +204,24 @@ __device__ __forceinline__ float vmf_scaled_norm(float k) {
 __device__ __forceinline__ float vmf_eval(const Lobe& L, float cn, float wx, float wy, float wz) {
     float d = L.mu[0] * wx + L.mu[1] * wy + L.mu[2] * wz;
     return cn * expf(L.kap * (d - 1.0f));
+}
+
+// Forward-path variants: 1 - e^{-2k} by its series below k = 0.05 (truncation
+// < 3e-8 relative), by the hardware exponential above; the lobe value by the
+// hardware exponential of kappa (mu.w - 1) <= 0.
+__device__ __forceinline__ float vmf_scaled_norm_fast(float k) {
+    float em;
+    if (k < 0.05f)
+        em = k * (2.0f + k * (-2.0f + k * (4.0f / 3.0f + k * (-2.0f / 3.0f + k * (4.0f / 15.0f)))));
+    else
+        em = 1.0f - __expf(-2.0f * k);
+    if (k < 1e-6f) return (1.0f + k) * kInv4Pi;
+    return __fdividef(k, 2.0f * kPi * em);
+}
+
+__device__ __forceinline__ float vmf_eval_fast(const Lobe& L, float cn, float wx, float wy, float wz) {
+    const float d = L.mu[0] * wx + L.mu[1] * wy + L.mu[2] * wz;
+    return cn * __expf(L.kap * (d - 1.0f));
 }
 
 // One minus the cosine to the mean, t = 1 - W, by inversion of the vMF
@@ -198,8 +251,11 @@ __device__ __forceinline__ void vmf_sample(const Lobe& L, float u1, float u2, fl
     const float t1 = vmf_sample_t(L.kap, u1);
     const float W = 1.0f - t1;
     const float s = sqrtf(t1 * (2.0f - t1));
+    // azimuth 2 pi u2 = pi + 2 pi (u2 - 1/2): hardware sine/cosine on [-pi, pi)
     float sp, cp;
-    sincosf(2.0f * kPi * u2, &sp, &cp);
+    __sincosf(2.0f * kPi * (u2 - 0.5f), &sp, &cp);
+    sp = -sp;
+    cp = -cp;
     float lx = s * cp, ly = s * sp;
     float t[3], b[3];
     frame(L.mu, t, b);
@@ -211,7 +267,9 @@ __device__ __forceinline__ void uniform_sphere(float u1, float u2, float out[3])
     float z = 1.0f - 2.0f * u1;
     float r = sqrtf(fmaxf(0.0f, 1.0f - z * z));
     float sp, cp;
-    sincosf(2.0f * kPi * u2, &sp, &cp);
+    __sincosf(2.0f * kPi * (u2 - 0.5f), &sp, &cp);
+    sp = -sp;
+    cp = -cp;
     out[0] = r * cp;
     out[1] = r * sp;
     out[2] = z;

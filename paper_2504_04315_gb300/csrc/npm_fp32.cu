@@ -250,7 +250,7 @@ __device__ __forceinline__ void decode_half(const DevCfg& cfg, const float* raw,
 #pragma unroll
     for (int ii = 0; ii < KH; ++ii)
         if (ii < hm.cnt) {
-            hm.lob[ii].lam = expf(raw[4 * (hm.l0 + ii)] - mx);
+            hm.lob[ii].lam = __expf(raw[4 * (hm.l0 + ii)] - mx);
             ssum += hm.lob[ii].lam;
         }
     ssum += __shfl_xor_sync(kFull, ssum, 1);
@@ -261,9 +261,9 @@ __device__ __forceinline__ void decode_half(const DevCfg& cfg, const float* raw,
             const int i = hm.l0 + ii;
             hm.lob[ii].lam *= inv;
             float th, ph;
-            decode_lobe(cfg.kappa_act, raw[4 * i + 1], raw[4 * i + 2], raw[4 * i + 3], hm.lob[ii],
+            decode_lobe_fast(cfg.kappa_act, raw[4 * i + 1], raw[4 * i + 2], raw[4 * i + 3], hm.lob[ii],
                         &th, &ph);
-            hm.cn[ii] = vmf_scaled_norm(hm.lob[ii].kap);
+            hm.cn[ii] = vmf_scaled_norm_fast(hm.lob[ii].kap);
             if (mix_out && valid) {
                 mix_out[(4 * i + 0) * ld + j] = hm.lob[ii].lam;
                 mix_out[(4 * i + 1) * ld + j] = hm.lob[ii].kap;
@@ -278,7 +278,7 @@ __device__ __forceinline__ float half_pdf(const HalfMix<KH>& hm, const float w[3
     float pv = 0.0f;
 #pragma unroll
     for (int ii = 0; ii < KH; ++ii)
-        if (ii < hm.cnt) pv += hm.lob[ii].lam * vmf_eval(hm.lob[ii], hm.cn[ii], w[0], w[1], w[2]);
+        if (ii < hm.cnt) pv += hm.lob[ii].lam * vmf_eval_fast(hm.lob[ii], hm.cn[ii], w[0], w[1], w[2]);
     return pv + __shfl_xor_sync(kFull, pv, 1);
 }
 

@@ -77,6 +77,7 @@ struct npm_server {
     std::map<int64_t, int64_t> free_list;  // offset -> length
     uint64_t next_id = 1;
     bool stop = false;
+    bool hold = false;
     int inflight = 0;
     std::thread worker;
 
@@ -248,7 +249,7 @@ void worker_loop(npm_server* s) {
     cudaSetDevice(s->h->device);
     std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
-        s->cv_work.wait(lk, [s] { return s->stop || !s->pending.empty(); });
+        s->cv_work.wait(lk, [s] { return s->stop || (!s->hold && !s->pending.empty()); });
         if (s->pending.empty()) {
             if (s->stop) break;
             continue;
@@ -385,6 +386,16 @@ npm_status npm_server_wait(npm_server* s, uint64_t ticket, double* latency_ms) {
     return NPM_OK;
 }
 
+npm_status npm_server_hold(npm_server* s, int hold) {
+    if (!s) return npm::set_error(NPM_ERR_INVALID_ARG, "server is NULL");
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->hold = hold != 0;
+    }
+    s->cv_work.notify_all();
+    return NPM_OK;
+}
+
 npm_status npm_server_get_stats(npm_server* s, npm_server_stats* out) {
     if (!s || !out) return npm::set_error(NPM_ERR_INVALID_ARG, "bad argument");
     std::lock_guard<std::mutex> lk(s->mu);
@@ -410,6 +421,7 @@ npm_status npm_server_destroy(npm_server* s) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
+        s->hold = false;
     }
     s->cv_work.notify_all();
     s->worker.join();

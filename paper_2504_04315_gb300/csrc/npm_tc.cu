@@ -290,7 +290,7 @@ __device__ __forceinline__ void tc_decode(const TcCfg& tc, const float (&raw)[4 
 #pragma unroll
     for (int i = 0; i < KMAX; ++i)
         if (i < K) {
-            lob[i].lam = expf(raw[4 * i] - mx);
+            lob[i].lam = __expf(raw[4 * i] - mx);
             ssum += lob[i].lam;
         }
     const float inv = 1.0f / ssum;
@@ -299,8 +299,8 @@ __device__ __forceinline__ void tc_decode(const TcCfg& tc, const float (&raw)[4 
         if (i < K) {
             lob[i].lam *= inv;
             float th, ph;
-            decode_lobe(cfg.kappa_act, raw[4 * i + 1], raw[4 * i + 2], raw[4 * i + 3], lob[i], &th, &ph);
-            cn[i] = vmf_scaled_norm(lob[i].kap);
+            decode_lobe_fast(cfg.kappa_act, raw[4 * i + 1], raw[4 * i + 2], raw[4 * i + 3], lob[i], &th, &ph);
+            cn[i] = vmf_scaled_norm_fast(lob[i].kap);
             if (mix_out && valid) {
                 mix_out[(4 * i + 0) * ld + j] = lob[i].lam;
                 mix_out[(4 * i + 1) * ld + j] = lob[i].kap;
@@ -348,7 +348,7 @@ __device__ __forceinline__ void tc_decode(const TcCfg& tc, const float (&raw)[4 
     float pv = 0.0f;
 #pragma unroll
     for (int i = 0; i < KMAX; ++i)
-        if (i < K) pv += lob[i].lam * vmf_eval(lob[i], cn[i], w[0], w[1], w[2]);
+        if (i < K) pv += lob[i].lam * vmf_eval_fast(lob[i], cn[i], w[0], w[1], w[2]);
     if (sample && ufrac > 0.0f) pv = ufrac * kInv4Pi + (1.0f - ufrac) * pv;
     if (valid) {
         if (sample) {

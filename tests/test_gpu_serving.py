@@ -48,7 +48,10 @@ def test_same_alone_and_in_the_mix(precision):
             srv.wait(srv.submit_query(*r))
             alone.append((r[2].numpy().copy(), r[3].numpy().copy()))
         mixed = [_req(n, 100 + i) for i, n in enumerate(sizes)]
+        # Queue them while admission is held, so that they share launches.
+        srv.hold(True)
         tickets = [srv.submit_query(*r) for r in mixed]
+        srv.hold(False)
         for t in tickets:
             srv.wait(t)
         st = srv.stats()
