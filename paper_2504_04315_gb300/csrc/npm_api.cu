@@ -435,11 +435,15 @@ npm_status npm_eval_pdf(npm_handle* h, int64_t n, const float* pos, const float*
 static npm_status backward_impl(npm_handle* h, int64_t n, const float* pos, const float* aux,
                                 const float* dir, const float* rad, const float* spdf,
                                 const float* dlogv, int64_t ld, cudaStream_t st) {
-    if (h->train_smem > 227 * 1024)
+    if (!npm::tc_can_train(h) && h->train_smem > 227 * 1024)
         return fail(NPM_ERR_UNSUPPORTED, "training activations do not fit in shared memory");
     float* loss_acc = h->scalars;
     NPM_CUDA(cudaMemsetAsync(loss_acc, 0, sizeof(float), st), "clear loss");
     if (n == 0) return NPM_OK;
+    if (npm::tc_can_train(h)) {
+        NPM_CUDA(npm::tc_train(h, n, ld, pos, aux, dir, rad, spdf, dlogv, loss_acc, st), "train launch");
+        return NPM_OK;
+    }
     NPM_CUDA(npm::launch_train_fp32(h->dc, h->params, h->mlp_off, h->wfwd, h->wbwd, n, ld, pos, aux,
                                     dir, rad, spdf, dlogv, h->grads, loss_acc, st),
              "train launch");

@@ -23,6 +23,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "npm_handle.h"
 #include "npm_kernels.h"
 
@@ -193,7 +195,19 @@ __device__ __forceinline__ void store_one(uint8_t* sA, uint32_t off, float a, ui
 // --------------------------------------------------------------- encode
 
 // Thread t writes row t of A (BF16, kp columns) for its query.
-__device__ __forceinline__ void tc_encode(const TcCfg& tc, const __half* __restrict__ grid_h,
+// Table entry loads: FP16 copy (inference) or FP32 master (training).
+__device__ __forceinline__ float2 load_feat2(const __half* g, uint32_t idx) {
+    const uint32_t raw = __ldg(reinterpret_cast<const unsigned int*>(g) + idx);
+    return __half22float2(*reinterpret_cast<const __half2*>(&raw));
+}
+__device__ __forceinline__ float2 load_feat2(const float* g, uint32_t idx) {
+    return __ldg(reinterpret_cast<const float2*>(g) + idx);
+}
+__device__ __forceinline__ float load_feat(const __half* e, int f) { return __half2float(e[f]); }
+__device__ __forceinline__ float load_feat(const float* e, int f) { return __ldg(e + f); }
+
+template <typename GT>
+__device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict__ grid_h,
                                           int64_t j, bool valid, int64_t ld,
                                           const float* __restrict__ pos,
                                           const float* __restrict__ aux, uint8_t* sA, int row) {
@@ -209,19 +223,17 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const __half* __restr
     const int F = cfg.feat;
     for (int l = 0; l < cfg.n_levels; ++l) {
         const Cell cl = make_cell(x, y, z, cfg.level_res[l]);
-        const __half* gl = grid_h + (size_t)cfg.level_off[l] * F;
+        const GT* gl = grid_h + (size_t)cfg.level_off[l] * F;
         if (F == 2) {
             float s0 = 0.0f, s1 = 0.0f;
-            uint32_t raw[8];
+            float2 v[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-                raw[c] = __ldg(reinterpret_cast<const unsigned int*>(gl) + corner_index(cfg, l, cl, c));
+            for (int c = 0; c < 8; ++c) v[c] = load_feat2(gl, corner_index(cfg, l, cl, c));
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const float w = corner_weight(cl, c);
-                const float2 v = __half22float2(*reinterpret_cast<const __half2*>(&raw[c]));
-                s0 = fmaf(w, v.x, s0);
-                s1 = fmaf(w, v.y, s1);
+                s0 = fmaf(w, v[c].x, s0);
+                s1 = fmaf(w, v[c].y, s1);
             }
             store_pair(sA, tile_off(row, 2 * l, kp), s0, s1, lo);
         } else {
@@ -231,10 +243,10 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const __half* __restr
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const float w = corner_weight(cl, c);
-                const __half* e = gl + (size_t)corner_index(cfg, l, cl, c) * F;
+                const GT* e = gl + (size_t)corner_index(cfg, l, cl, c) * F;
 #pragma unroll
                 for (int f = 0; f < 8; ++f)
-                    if (f < F) s[f] = fmaf(w, __half2float(e[f]), s[f]);
+                    if (f < F) s[f] = fmaf(w, load_feat(e, f), s[f]);
             }
 #pragma unroll
             for (int f = 0; f < 8; f += 2)
@@ -521,6 +533,356 @@ __global__ void k_tc_weights(TcCfg tc, const float* __restrict__ mlp, uint8_t* _
     }
 }
 
+// ----------------------------------------------------------- training
+
+// Training layout: per layer the input activation tile H_l (BF16, K-major,
+// 128 x Kp_l) at h_off, the delta tile D (BF16, K-major, 128 x 128) at
+// d_off; TMEM columns [0, c0) hold the forward / input-gradient
+// accumulator and [dw_col_l, dw_col_l + Kp_l) the weight gradient of
+// layer l, accumulated over all tiles of the CTA.
+struct TcTrain {
+    uint32_t h_off[NPM_MAX_LAYERS];
+    uint32_t dw_col[NPM_MAX_LAYERS];
+    uint32_t idesc_dw[NPM_MAX_LAYERS];  // A MN-major, B MN-major, N = Kp_l
+    uint32_t idesc_dx[NPM_MAX_LAYERS];  // A K-major,  B MN-major, N = Kp_l
+    uint32_t d_off, bar_off, smem, tmem_cols;
+    int64_t woff[NPM_MAX_LAYERS];       // packed offset of W_l in the MLP region
+    int split;                          // BF16 residual operands (three MMAs per K step)
+    uint32_t hlo_off;                   // residual of the current layer's input tile
+    uint32_t dlo_off;                   // residual of the delta tile
+};
+
+// d log V / d raw for one query (all K lobes in this thread), in the log
+// domain; returns s * log V and writes s * d log V / d raw to d[].
+template <int KMAX>
+__device__ __forceinline__ float tc_grad_raw(const DevCfg& cfg, const float (&raw)[4 * KMAX], const float w[3],
+                                             float s, float (&d)[4 * KMAX]) {
+    const int K = cfg.K;
+    float mx = -INFINITY;
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i)
+        if (i < K) mx = fmaxf(mx, raw[4 * i]);
+    float ssum = 0.0f;
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i)
+        if (i < K) ssum += expf(raw[4 * i] - mx);
+    const float lse = mx + logf(ssum);
+    float a[KMAX], kap[KMAX], md[KMAX], wdt[KMAX], wdp[KMAX], sk[KMAX], st[KMAX], sp[KMAX], lp[KMAX];
+    float amax = -INFINITY;
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i)
+        if (i < K) {
+            lp[i] = raw[4 * i] - lse;
+            const float rk = raw[4 * i + 1];
+            if (cfg.kappa_act == NPM_EXP) {
+                kap[i] = expf(rk);
+                sk[i] = kap[i];
+            } else {
+                kap[i] = softplus(rk);
+                sk[i] = logistic(rk);
+            }
+            st[i] = logistic(raw[4 * i + 2]);
+            sp[i] = logistic(raw[4 * i + 3]);
+            float sth, cth, sph, cph;
+            sincosf(kPi * st[i], &sth, &cth);
+            sincosf(2.0f * kPi * sp[i], &sph, &cph);
+            md[i] = sth * cph * w[0] + sth * sph * w[1] + cth * w[2];
+            wdt[i] = cth * cph * w[0] + cth * sph * w[1] - sth * w[2];
+            wdp[i] = -sth * sph * w[0] + sth * cph * w[1];
+            a[i] = lp[i] + logf(vmf_scaled_norm(kap[i])) + kap[i] * (md[i] - 1.0f);
+            amax = fmaxf(amax, a[i]);
+        }
+    float es = 0.0f;
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i)
+        if (i < K) es += expf(a[i] - amax);
+    const float logV = amax + logf(es);
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) {
+        if (i < K) {
+            const float r = expf(a[i] - logV);
+            const float lam = expf(lp[i]);
+            const float sr = s * r;
+            d[4 * i + 0] = s * (r - lam);
+            d[4 * i + 1] = sr * (inv_minus_coth(kap[i]) + md[i]) * sk[i];
+            d[4 * i + 2] = sr * kap[i] * wdt[i] * kPi * st[i] * (1.0f - st[i]);
+            d[4 * i + 3] = sr * kap[i] * wdp[i] * 2.0f * kPi * sp[i] * (1.0f - sp[i]);
+        } else {
+            d[4 * i + 0] = d[4 * i + 1] = d[4 * i + 2] = d[4 * i + 3] = 0.0f;
+        }
+    }
+    return s * logV;
+}
+
+// Stores 16 values as BF16 at row t, columns c0 .. c0+15 of a K-major tile.
+__device__ __forceinline__ void store16_plain(uint8_t* base, int t, int c0, int kp, const float* v) {
+    uint32_t h[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) h[i] = pack_bf16(v[2 * i], v[2 * i + 1]);
+    *reinterpret_cast<uint4*>(base + tile_off(t, c0, kp)) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(base + tile_off(t, c0 + 8, kp)) = make_uint4(h[4], h[5], h[6], h[7]);
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(kThreads, 1) k_train_tc(
+    const __grid_constant__ TcCfg tc, const __grid_constant__ TcTrain tt, const float* __restrict__ grid32,
+    const uint8_t* __restrict__ wblob, int64_t n, int64_t ld, const float* __restrict__ pos,
+    const float* __restrict__ aux, const float* __restrict__ dir, const float* __restrict__ rad,
+    const float* __restrict__ spdf, const float* __restrict__ dlogv, float inv_n, float* __restrict__ grad,
+    int64_t mlp_off, float* __restrict__ loss, int* __restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sW = smem;
+    uint8_t* sD = smem + tt.d_off;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + tt.bar_off);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
+    const int t = threadIdx.x, warp = t >> 5;
+    const uint32_t bar_mma = smem_u32(&bars[0]), bar_w = smem_u32(&bars[1]);
+    const DevCfg& cfg = tc.base;
+    const int L = cfg.n_layers;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(tt.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (t == 0) {
+        mbar_init(bar_mma, 1);
+        mbar_init(bar_w, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_async_smem();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t wbytes = (tt.split ? 2u : 1u) * tc.w_bytes;
+    if (t == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_w), "r"(wbytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_u32(sW)),
+                     "l"(wblob), "r"(wbytes), "r"(bar_w)
+                     : "memory");
+    }
+    bool ok = !__syncthreads_or(!mbar_wait_bounded(bar_w, 0));
+    uint32_t phase = 0;
+    const uint32_t sW_addr = smem_u32(sW), sD_addr = smem_u32(sD), base_addr = smem_u32(smem);
+    const uint32_t wlo = tc.w_bytes;                      // residual weights follow the high parts
+    const uint32_t hlo_addr = base_addr + tt.hlo_off, dlo_addr = base_addr + tt.dlo_off;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    float lacc = 0.0f;
+    bool first = true;
+    const int64_t ntiles = (n + kTile - 1) / kTile;
+    for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        const int64_t j = tile * kTile + t;
+        const bool valid = j < n;
+        tc_encode(tc, grid32, j, valid, ld, pos, aux, smem + tt.h_off[0], t);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        float raw[4 * KMAX];
+        // Forward, keeping every layer's input tile.
+        for (int l = 0; l < L && ok; ++l) {
+            const TcLayer& ly = tc.layer[l];
+            if (t == 0) {
+                tc_fence_after();
+                const uint32_t sbo = (uint32_t)(ly.Kp >> 3) * 128u;
+                for (int s = 0; s < (ly.Kp >> 4); ++s) {
+                    const uint64_t ad = umma_desc(base_addr + tt.h_off[l] + s * 256u, 128u, sbo);
+                    const uint64_t bd = umma_desc(sW_addr + ly.w_off + s * 256u, 128u, sbo);
+                    mma_bf16(tmem, ad, bd, ly.idesc, s > 0 ? 1u : 0u);
+                    if (tt.split) {
+                        mma_bf16(tmem, ad, umma_desc(sW_addr + wlo + ly.w_off + s * 256u, 128u, sbo), ly.idesc, 1u);
+                        mma_bf16(tmem, umma_desc(hlo_addr + s * 256u, 128u, sbo), bd, ly.idesc, 1u);
+                    }
+                }
+                mma_commit(bar_mma);
+            }
+            const bool done = mbar_wait_bounded(bar_mma, phase);
+            phase ^= 1u;
+            ok = !__syncthreads_or(!done);
+            if (!ok) break;
+            tc_fence_after();
+            if (l < L - 1) {
+                uint8_t* hn = smem + tt.h_off[l + 1];
+                const int kpn = tc.layer[l + 1].Kp;
+                const uint32_t lo = tt.split ? tt.hlo_off - tt.h_off[l + 1] : 0u;
+                for (int c0 = 0; c0 < ly.Np; c0 += 16) {
+                    uint32_t r[16];
+                    tmem_ld16(tmem + lane_base + (uint32_t)c0, r);
+                    tmem_wait16(r);
+                    float v[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = fmaxf(__uint_as_float(r[i]), 0.0f);
+                    store16(hn, tile_off(t, c0, kpn), tile_off(t, c0 + 8, kpn), v, lo);
+                }
+                fence_async_smem();
+                tc_fence_before();
+                __syncthreads();
+            } else {
+                uint32_t r[4 * KMAX / 16][16];
+#pragma unroll
+                for (int c = 0; c < 4 * KMAX / 16; ++c)
+                    if (c * 16 < ly.Np) tmem_ld16(tmem + lane_base + (uint32_t)(c * 16), r[c]);
+#pragma unroll
+                for (int c = 0; c < 4 * KMAX / 16; ++c)
+                    if (c * 16 < ly.Np) tmem_wait16(r[c]);
+#pragma unroll
+                for (int c = 0; c < 4 * KMAX / 16; ++c)
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) raw[c * 16 + i] = __uint_as_float(r[c][i]);
+            }
+        }
+        if (!ok) break;
+        // Loss and d loss / d raw (zero for rows beyond n).
+        float w[3] = {0.0f, 0.0f, 1.0f}, sc = 0.0f;
+        if (valid) {
+            w[0] = dir[j];
+            w[1] = dir[ld + j];
+            w[2] = dir[2 * ld + j];
+            sc = dlogv ? dlogv[j] : -(rad[j] / spdf[j]) * inv_n;
+        }
+        float dr[4 * KMAX];
+        const float lv = tc_grad_raw<KMAX>(cfg, raw, w, sc, dr);
+        if (valid) lacc += lv;
+        const int np_last = tc.layer[L - 1].Np;
+        const uint32_t dlo = tt.split ? tt.dlo_off - tt.d_off : 0u;
+#pragma unroll
+        for (int c = 0; c < 4 * KMAX / 16; ++c)
+            if (c * 16 < np_last) {
+                float v[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = dr[c * 16 + i];
+                store16(sD, tile_off(t, c * 16, 128), tile_off(t, c * 16 + 8, 128), v, dlo);
+            }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        // Backward, top layer first.
+        for (int l = L - 1; l >= 0 && ok; --l) {
+            const TcLayer& ly = tc.layer[l];
+            if (t == 0) {
+                tc_fence_after();
+                const uint32_t hk = (uint32_t)(ly.Kp >> 3) * 128u;  // K step of an H_l / W_l tile
+                // dW_l += D^T H_l: M = 128 (outputs), N = Kp_l, K = 128 samples.
+                for (int s = 0; s < 8; ++s) {
+                    const uint64_t bh = umma_desc(base_addr + tt.h_off[l] + s * 2u * hk, hk, 128u);
+                    mma_bf16(tmem + tt.dw_col[l], umma_desc(sD_addr + s * 2u * 2048u, 2048u, 128u), bh,
+                             tt.idesc_dw[l], (first && s == 0) ? 0u : 1u);
+                    if (tt.split)
+                        mma_bf16(tmem + tt.dw_col[l], umma_desc(dlo_addr + s * 2u * 2048u, 2048u, 128u), bh,
+                                 tt.idesc_dw[l], 1u);
+                }
+                // D W_l: M = 128 samples, N = Kp_l, K = Np_l outputs.
+                for (int s = 0; s < (ly.Np >> 4); ++s) {
+                    const uint64_t ad = umma_desc(sD_addr + s * 256u, 128u, 2048u);
+                    const uint64_t bd = umma_desc(sW_addr + ly.w_off + s * 2u * hk, hk, 128u);
+                    mma_bf16(tmem, ad, bd, tt.idesc_dx[l], s > 0 ? 1u : 0u);
+                    if (tt.split) {
+                        mma_bf16(tmem, ad, umma_desc(sW_addr + wlo + ly.w_off + s * 2u * hk, hk, 128u),
+                                 tt.idesc_dx[l], 1u);
+                        mma_bf16(tmem, umma_desc(dlo_addr + s * 256u, 128u, 2048u), bd, tt.idesc_dx[l], 1u);
+                    }
+                }
+                mma_commit(bar_mma);
+            }
+            const bool done = mbar_wait_bounded(bar_mma, phase);
+            phase ^= 1u;
+            ok = !__syncthreads_or(!done);
+            if (!ok) break;
+            tc_fence_after();
+            const uint8_t* hl = smem + tt.h_off[l];
+            if (l > 0) {
+                // delta_{l-1} = (D W_l) masked by ReLU'(z_{l-1}) (H_l > 0).
+                for (int c0 = 0; c0 < ly.Kp; c0 += 16) {
+                    uint32_t r[16];
+                    tmem_ld16(tmem + lane_base + (uint32_t)c0, r);
+                    tmem_wait16(r);
+                    const uint4 m0 = *reinterpret_cast<const uint4*>(hl + tile_off(t, c0, ly.Kp));
+                    const uint4 m1 = *reinterpret_cast<const uint4*>(hl + tile_off(t, c0 + 8, ly.Kp));
+                    const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+                    float v[16];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float2 hv = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&mw[i]));
+                        v[2 * i] = hv.x > 0.0f ? __uint_as_float(r[2 * i]) : 0.0f;
+                        v[2 * i + 1] = hv.y > 0.0f ? __uint_as_float(r[2 * i + 1]) : 0.0f;
+                    }
+                    store16(sD, tile_off(t, c0, 128), tile_off(t, c0 + 8, 128), v, dlo);
+                }
+                fence_async_smem();
+                tc_fence_before();
+                __syncthreads();
+            } else {
+                // Encoder gradient -> grid scatter (Eq. 11 transposed).
+                float dg[32];
+                for (int c0 = 0; c0 < cfg.grid_feats && c0 < 32; c0 += 16) {
+                    uint32_t r[16];
+                    tmem_ld16(tmem + lane_base + (uint32_t)c0, r);
+                    tmem_wait16(r);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) dg[c0 + i] = __uint_as_float(r[i]);
+                }
+                tc_fence_before();
+                if (valid) {
+                    const float x = pos[j], y = pos[ld + j], z = pos[2 * ld + j];
+                    const int F = cfg.feat;
+                    for (int lv2 = 0; lv2 < cfg.n_levels; ++lv2) {
+                        const Cell cl = make_cell(x, y, z, cfg.level_res[lv2]);
+                        float* gl = grad + (size_t)cfg.level_off[lv2] * F;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const float wc = corner_weight(cl, c);
+                            float* e = gl + (size_t)corner_index(cfg, lv2, cl, c) * F;
+                            if (F == 2) {
+                                atomicAdd(reinterpret_cast<float2*>(e),
+                                          make_float2(wc * dg[lv2 * 2], wc * dg[lv2 * 2 + 1]));
+                            } else if (F == 4) {
+                                atomicAdd(reinterpret_cast<float4*>(e),
+                                          make_float4(wc * dg[lv2 * 4], wc * dg[lv2 * 4 + 1], wc * dg[lv2 * 4 + 2],
+                                                      wc * dg[lv2 * 4 + 3]));
+                            } else {
+                                for (int f = 0; f < F; ++f) atomicAdd(e + f, wc * dg[lv2 * F + f]);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        first = false;
+    }
+    // Loss: one atomic per warp.
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lacc += __shfl_xor_sync(0xffffffffu, lacc, o);
+    if ((t & 31) == 0 && lacc != 0.0f) atomicAdd(loss, lacc);
+    // Weight gradients: lane o of layer l's TMEM region holds dW_l[o][*].
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (ok && !first) {
+        for (int l = 0; l < L; ++l) {
+            const TcLayer& ly = tc.layer[l];
+            const int o = warp * 32 + (t & 31);
+            float* gW = grad + mlp_off + tt.woff[l];
+            for (int c0 = 0; c0 < ly.Kp; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(tmem + lane_base + tt.dw_col[l] + (uint32_t)c0, r);
+                tmem_wait16(r);
+                if (o < ly.N)
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (c0 + i < ly.K) atomicAdd(gW + (int64_t)o * ly.K + c0 + i, __uint_as_float(r[i]));
+            }
+        }
+    }
+    if (!ok && t == 0) atomicOr(status, kStatusTimeout);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tt.tmem_cols) : "memory");
+    }
+}
+
 }  // namespace
 
 struct TcState {
@@ -528,6 +890,9 @@ struct TcState {
     uint8_t* wblob = nullptr;
     size_t smem = 0;
     int grid = 0;
+    TcCfg train_cfg;     // single-pass BF16 copy of cfg for training
+    TcTrain train;
+    bool can_train = false;
 };
 
 static int pad16(int v) { return (v + 15) / 16 * 16; }
@@ -570,6 +935,53 @@ npm_status tc_create(npm_handle* h) {
     if (s->smem > 200 * 1024 || c.K > 16) {
         delete s;
         return NPM_ERR_UNSUPPORTED;
+    }
+    // Training layout (single-pass BF16 operands).
+    {
+        TcTrain& tr = s->train;
+        memset(&tr, 0, sizeof(tr));
+        s->train_cfg = t;
+        uint32_t off = (c.precision == NPM_BF16X3 ? 2u : 1u) * t.w_bytes, col0 = 0, cols = 0;
+        int64_t wo = 0;
+        bool fits = c.K * 4 <= 64 && c.n_levels * c.feat_per_level <= 32;
+        for (int l = 0; l < c.n_layers; ++l) {
+            const TcLayer& ly = t.layer[l];
+            tr.h_off[l] = off;
+            off += (uint32_t)(kTile * ly.Kp * 2);
+            col0 = (uint32_t)std::max<int>((int)col0, std::max(ly.Kp, ly.Np));
+            tr.woff[l] = wo;
+            wo += (int64_t)ly.K * ly.N;
+            if (ly.Np > 128 || ly.Kp > 128) fits = false;
+            // dW: A = delta^T (MN-major), B = H_l (MN-major), M = 128, N = Kp_l.
+            tr.idesc_dw[l] = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                             ((uint32_t)(ly.Kp >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+            // dX: A = delta (K-major), B = W_l read MN-major, M = 128, N = Kp_l.
+            tr.idesc_dx[l] = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) |
+                             ((uint32_t)(ly.Kp >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+        }
+        tr.split = c.precision == NPM_BF16X3 ? 1 : 0;
+        int maxkp = 0;
+        for (int l = 0; l < c.n_layers; ++l) maxkp = std::max(maxkp, t.layer[l].Kp);
+        tr.hlo_off = off;  // one residual activation tile, reused layer by layer
+        if (tr.split) off += (uint32_t)(kTile * maxkp * 2);
+        // The encoder writes its residual at (tile + a_bytes): point that at
+        // the shared residual tile.
+        s->train_cfg.split = tr.split;
+        s->train_cfg.a_bytes = tr.split ? tr.hlo_off - tr.h_off[0] : 0u;
+        col0 = (col0 + 15) / 16 * 16;
+        cols = col0;
+        for (int l = 0; l < c.n_layers; ++l) {
+            tr.dw_col[l] = cols;
+            cols += (uint32_t)t.layer[l].Kp;
+        }
+        uint32_t pw = 32;
+        while (pw < cols) pw <<= 1;
+        tr.tmem_cols = pw;
+        tr.d_off = (off + 127u) / 128u * 128u;
+        tr.dlo_off = tr.d_off + kTile * 128 * 2;
+        tr.bar_off = tr.dlo_off + (tr.split ? kTile * 128 * 2 : 0);
+        tr.smem = tr.bar_off + 64;
+        s->can_train = fits && pw <= 512 && tr.smem <= 220 * 1024;
     }
     if (cudaMalloc(&s->wblob, nsplit * t.w_bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -632,6 +1044,39 @@ static cudaError_t launch_tc(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaS
     int* status = reinterpret_cast<int*>(h->scalars + 8);
     kern<<<(int)g, kThreads, s->smem, st>>>(s->cfg, h->grid_h, s->wblob, qb, status);
     return cudaGetLastError();
+}
+
+template <int KMAX>
+static cudaError_t launch_train_tc(npm_handle* h, int64_t n, int64_t ld, const float* pos, const float* aux,
+                                   const float* dir, const float* rad, const float* spdf, const float* dlogv,
+                                   float* loss, cudaStream_t st) {
+    TcState* s = h->tc;
+    auto kern = k_train_tc<KMAX>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->train.smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             carveout_percent(s->train.smem + 1024));
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t ntiles = (n + kTile - 1) / kTile;
+    const int g = (int)(ntiles < sms ? ntiles : sms);
+    int* status = reinterpret_cast<int*>(h->scalars + 8);
+    kern<<<g < 1 ? 1 : g, kThreads, s->train.smem, st>>>(s->train_cfg, s->train, h->params, s->wblob, n, ld, pos,
+                                                         aux, dir, rad, spdf, dlogv, 1.0f / (float)n, h->grads,
+                                                         h->mlp_off, loss, status);
+    return cudaGetLastError();
+}
+
+bool tc_can_train(npm_handle* h) { return h->tc && h->tc->can_train; }
+
+cudaError_t tc_train(npm_handle* h, int64_t n, int64_t ld, const float* pos, const float* aux, const float* dir,
+                     const float* rad, const float* spdf, const float* dlogv, float* loss, cudaStream_t st) {
+    const int K = h->cfg.K;
+    if (K <= 4) return launch_train_tc<4>(h, n, ld, pos, aux, dir, rad, spdf, dlogv, loss, st);
+    if (K <= 8) return launch_train_tc<8>(h, n, ld, pos, aux, dir, rad, spdf, dlogv, loss, st);
+    return launch_train_tc<16>(h, n, ld, pos, aux, dir, rad, spdf, dlogv, loss, st);
 }
 
 cudaError_t tc_query_batch(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStream_t st) {

@@ -119,3 +119,41 @@ def test_tc_matches_fp32_path_on_lobe_choice():
     ang = np.linalg.norm(host(db) - host(df), axis=0)
     assert np.median(ang) < 2e-2
     assert (ang > 0.5).mean() < 2e-2
+
+
+@pytest.mark.parametrize("w,n", [(synth.TINY_BF16, 4096), (PRODUCT_SMALL.with_(precision=synth.BF16X3), 4096),
+                                 (synth.PAPER_HASH.with_(precision=synth.BF16X3), 4096),
+                                 (synth.PRODUCT_BF16, 3000),
+                                 (synth.TINY_BF16.with_(precision=synth.BF16), 4096)])
+def test_tc_gradient_parity(w, n):
+    # Training on tensor cores (FP32 TMEM accumulation, FP16 grid features)
+    # against the FP64 oracle with the FP32 master parameters. Split BF16:
+    # per-tensor relative L2 <= 2e-2. Single-pass BF16 compounds its rounding
+    # down the layers and the grid sums cancel heavily: held to 0.3.
+    params = synth.random_params(w, 12)
+    b = synth.train_batch_uniform(w, n, seed=12)
+    m = make_model(w, params, n, precision=w.precision)
+    dlogv = -(b.radiance.astype(np.float64) / b.pdf) / n
+    m.backward(cuda(b.pos), cuda(b.dir), cuda(dlogv), None if b.aux is None else cuda(b.aux))
+    g = m.get_grads()
+    m.check_device_status()
+    loss, ref = oracle.train_grad(w, params, b.pos, b.dir, b.radiance, b.pdf, b.aux)
+    ng = sum(synth.grid_sizes(w)) * w.feat
+    blocks = [("grid", slice(0, ng))]
+    o = ng
+    for i in range(len(w.widths) - 1):
+        k = w.widths[i] * w.widths[i + 1]
+        blocks.append((f"W{i + 1}", slice(o, o + k)))
+        o += k
+    errs = {}
+    for name, sl in blocks:
+        errs[name] = np.linalg.norm(g[sl] - ref[sl]) / max(np.linalg.norm(ref[sl]), 1e-30)
+    print(f"tc grad rel L2 {w.name[:30]} precision {w.precision}: "
+          + ", ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+    bar = 2e-2 if w.precision == synth.BF16X3 else 0.3
+    assert max(errs.values()) <= bar, errs
+    # The training loss of the same batch through train_step.
+    m2 = make_model(w, params, n, precision=w.precision)
+    l2 = m2.train_step(cuda(b.pos), cuda(b.dir), cuda(b.radiance), cuda(b.pdf),
+                       None if b.aux is None else cuda(b.aux))
+    assert abs(float(host(l2)[0]) - loss) <= bar * abs(loss)
