@@ -136,7 +136,7 @@ def run_reference(args, w, rank):
         "value": v, "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "queries_per_step": n, "sample_of": w.n_query},
+        "config": {"workload": w.name, ("samples_per_step" if train_mode else "queries_per_step"): n, "sample_of": w.n_query},
         "cpu_baseline": {"value": v, "unit": "queries/s", "cores": cores, "kind": "oracle",
                          "sample": f"{n} queries per step of the {w.n_query}-query workload"},
         "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
@@ -174,6 +174,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="paper_hash", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--mode", default="query", choices=["query", "train"],
+                    help="timed step: one query call (queries/s) or one training step (samples/s)")
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-train", action="store_true")
@@ -198,23 +200,36 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    n = w.n_query
+    train_mode = args.mode == "train"
+    n = (w.n_train or w.n_query) if train_mode else w.n_query
     nrot = 8
     m = npm.NPM(npm.config_from(w, max_batch=n))
     params = synth.random_params(w, 3)
     m.set_params(params)
     seed0 = 1000 * rank
-    pos = [torch.from_numpy(synth.positions(seed0 + i, n)).cuda() for i in range(nrot)]
-    uu = [torch.from_numpy(synth.sample_uniforms(seed0 + i, n)).cuda() for i in range(nrot)]
-    aux = ([torch.from_numpy(synth.aux_inputs(seed0 + i, n)).cuda() for i in range(nrot)]
-           if w.mode == synth.PRODUCT else [None] * nrot)
-    outs = [(torch.empty((3, n), device="cuda"), torch.empty((n,), device="cuda"))
-            for _ in range(nrot)]
     stream = torch.cuda.current_stream()
+    if train_mode:
+        tbs = []
+        for i in range(2):
+            b = synth.train_batch_uniform(w, n, seed=seed0 + i)
+            tbs.append([torch.from_numpy(np.ascontiguousarray(a)).cuda() if a is not None else None
+                        for a in (b.pos, b.dir, b.radiance, b.pdf, b.aux)])
+        loss_buf = torch.zeros(1, device="cuda")
 
-    def step(i):
-        k = i % nrot
-        m.query_sample(pos[k], uu[k], aux[k], out=outs[k], stream=stream)
+        def step(i):
+            b = tbs[i % 2]
+            m.train_step(b[0], b[1], b[2], b[3], b[4], loss_out=loss_buf, stream=stream)
+    else:
+        pos = [torch.from_numpy(synth.positions(seed0 + i, n)).cuda() for i in range(nrot)]
+        uu = [torch.from_numpy(synth.sample_uniforms(seed0 + i, n)).cuda() for i in range(nrot)]
+        aux = ([torch.from_numpy(synth.aux_inputs(seed0 + i, n)).cuda() for i in range(nrot)]
+               if w.mode == synth.PRODUCT else [None] * nrot)
+        outs = [(torch.empty((3, n), device="cuda"), torch.empty((n,), device="cuda"))
+                for _ in range(nrot)]
+
+        def step(i):
+            k = i % nrot
+            m.query_sample(pos[k], uu[k], aux[k], out=outs[k], stream=stream)
 
     for i in range(args.warmup):
         step(i)
@@ -244,7 +259,7 @@ def main():
     # End to end through the host-buffer entry point: pinned inputs copied
     # in, results copied out, inside the timed region.
     e2e = None
-    if not args.no_extras:
+    if not args.no_extras and not train_mode:
         hpos = [torch.from_numpy(synth.positions(seed0 + i, n)).pin_memory() for i in range(2)]
         hu = [torch.from_numpy(synth.sample_uniforms(seed0 + i, n)).pin_memory() for i in range(2)]
         haux = ([torch.from_numpy(synth.aux_inputs(seed0 + i, n)).pin_memory() for i in range(2)]
@@ -362,24 +377,33 @@ def main():
     achieved = mlp_flops(w) * n / (kern_ms / 1e3) / 1e12
     per_sorted = sorted(per)
     line = {
-        "metric": "guided queries/s (encode+decode+sample+pdf)",
-        "value": value, "unit": "queries/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "metric": ("train samples/s (forward + backward + Adam)" if train_mode
+                   else "guided queries/s (encode+decode+sample+pdf)"),
+        "value": value, "unit": "samples/s" if train_mode else "queries/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if w.precision == synth.FP32 else "bf16",
+        "vs_baseline": None,
+        "dtype": {synth.FP32: "f32", synth.BF16: "bf16", synth.BF16X3: "bf16x3 (split bf16)"}[w.precision],
         "data": "synthetic (seeded positions/uniforms; parameters with kappa up to ~35)",
-        "config": {"workload": w.name, "queries_per_step": n,
-                   "l2": f"inputs rotate over {nrot} batches ({nrot * n * 40 / 1e6:.0f} MB incl. outputs) > L2",
+        "config": {"workload": w.name, ("samples_per_step" if train_mode else "queries_per_step"): n,
+                   "l2": (f"two training batches alternate ({2 * n * 40 / 1e6:.0f} MB) and every step "
+                          "streams the 167 MB Adam state" if train_mode else
+                          f"inputs rotate over {nrot} batches ({nrot * n * 40 / 1e6:.0f} MB incl. outputs) > L2"),
                    "parallelism": f"dp{world} (independent batches per GPU)"},
         "latency": {"p50_ms": per_sorted[len(per) // 2],
                     "p99_ms": per_sorted[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)],
-                    "unit": "ms per 2^20-query batch (the serving loop's per-bounce "
-                            "latencies are under serving)"},
+                    "unit": f"ms per {'training step' if train_mode else 'call'} of {n} "
+                            f"{'samples' if train_mode else 'queries'} (the serving loop's "
+                            "per-bounce latencies are under serving)"},
         "e2e": e2e,
-        "gpu_launches": K,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": achieved / alu_peak, "traffic": None,
-                     "kernel": "k_forward_fp32<sample>",
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"},
+        # Kernels per step: one fused query kernel; a training step launches
+        # the training kernel, Adam, the step counter, the FP32 weight
+        # arrangement, the loss copy, and on tensor cores the BF16 weights.
+        "gpu_launches": K * ((6 if w.precision != synth.FP32 else 5) if train_mode else 1),
+        "roofline": ({"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                      "frac": achieved / alu_peak, "traffic": None,
+                      "kernel": "k_forward_fp32<sample>",
+                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"}
+                     if (w.precision == synth.FP32 and not train_mode) else None),
         "clocks": clocks,
         "train": train,
         "reduced_precision": reduced,

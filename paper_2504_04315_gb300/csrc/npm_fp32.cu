@@ -57,11 +57,17 @@ __device__ __forceinline__ void tile_gemm(int t, const float* __restrict__ in, i
                                           float* __restrict__ out, int N, int mode,
                                           const float* __restrict__ mask) {
     const int g = t & 15, qg = t >> 4;
-    float acc[8][NI];
+    // Accumulators paired along adjacent outputs: one packed two-lane FMA
+    // (fma.rn on each lane, the same rounding as fmaf) per pair.
+    constexpr int NP2 = NI >= 2 ? NI / 2 : 1;
+    float2 acc[8][NP2];
+    float acc1[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
+    for (int j = 0; j < 8; ++j) {
+        acc1[j] = 0.0f;
 #pragma unroll
-        for (int i = 0; i < NI; ++i) acc[j][i] = 0.0f;
+        for (int i = 0; i < NP2; ++i) acc[j][i] = make_float2(0.0f, 0.0f);
+    }
     for (int k = 0; k < K; k += 4) {
         float4 a[8];
 #pragma unroll
@@ -72,9 +78,15 @@ __device__ __forceinline__ void tile_gemm(int t, const float* __restrict__ in, i
             load_w<NI>(WT + (k + kk) * NP + g * NI, w);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                float av = kk == 0 ? a[j].x : kk == 1 ? a[j].y : kk == 2 ? a[j].z : a[j].w;
+                const float av = kk == 0 ? a[j].x : kk == 1 ? a[j].y : kk == 2 ? a[j].z : a[j].w;
+                if constexpr (NI == 1) {
+                    acc1[j] = fmaf(av, w[0], acc1[j]);
+                } else {
+                    const float2 aa = make_float2(av, av);
 #pragma unroll
-                for (int i = 0; i < NI; ++i) acc[j][i] = fmaf(av, w[i], acc[j][i]);
+                    for (int i = 0; i < NP2; ++i)
+                        acc[j][i] = __ffma2_rn(aa, make_float2(w[2 * i], w[2 * i + 1]), acc[j][i]);
+                }
             }
         }
     }
@@ -85,7 +97,7 @@ __device__ __forceinline__ void tile_gemm(int t, const float* __restrict__ in, i
         for (int i = 0; i < NI; ++i) {
             const int n = g * NI + i;
             if (n < N) {
-                float v = acc[j][i];
+                float v = NI == 1 ? acc1[j] : ((i & 1) ? acc[j][i >> 1].y : acc[j][i >> 1].x);
                 if (mode == 1) v = fmaxf(v, 0.0f);
                 if (mode == 2) v = mask[row + n] > 0.0f ? v : 0.0f;
                 out[row + n] = v;
@@ -685,29 +697,46 @@ __global__ void k_adam(int64_t n4, float4* __restrict__ p, float4* __restrict__ 
     if (skip && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatusNumeric);
     const float t = (float)(*steps + 1);
     const float c1 = 1.0f - powf(b1, t), c2 = 1.0f - powf(b2, t);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        float4 gg = g[i];
-        g[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (skip) continue;
-        float4 mm = m[i], vv = v[i], pp = p[i];
-        float* pm = &mm.x;
-        float* pv = &vv.x;
-        float* pg = &gg.x;
-        float* pp_ = &pp.x;
+    // Two float4 groups per thread and iteration: more bytes in flight.
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n4; i0 += 2 * stride) {
+        float4 gg[2], mm[2], vv[2], pp[2];
+        bool in[2];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            pm[c] = b1 * pm[c] + (1.0f - b1) * pg[c];
-            pv[c] = b2 * pv[c] + (1.0f - b2) * pg[c] * pg[c];
-            const float mh = pm[c] / c1, vh = pv[c] / c2;
-            pp_[c] -= lr * mh / (sqrtf(vh) + eps);
+        for (int u = 0; u < 2; ++u) {
+            const int64_t i = i0 + u * stride;
+            in[u] = i < n4;
+            if (in[u]) {
+                gg[u] = g[i];
+                mm[u] = m[i];
+                vv[u] = v[i];
+                pp[u] = p[i];
+            }
         }
-        m[i] = mm;
-        v[i] = vv;
-        p[i] = pp;
-        if (half_copy && i < n_half4) {
-            half_copy[2 * i] = __floats2half2_rn(pp.x, pp.y);
-            half_copy[2 * i + 1] = __floats2half2_rn(pp.z, pp.w);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (!in[u]) continue;
+            g[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (skip) continue;
+            float* pm = &mm[u].x;
+            float* pv = &vv[u].x;
+            const float* pg = &gg[u].x;
+            float* pq = &pp[u].x;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                pm[c] = b1 * pm[c] + (1.0f - b1) * pg[c];
+                pv[c] = b2 * pv[c] + (1.0f - b2) * pg[c] * pg[c];
+                const float mh = pm[c] / c1, vh = pv[c] / c2;
+                pq[c] -= lr * mh / (sqrtf(vh) + eps);
+            }
+            m[i] = mm[u];
+            v[i] = vv[u];
+            p[i] = pp[u];
+            if (half_copy && i < n_half4) {
+                half_copy[2 * i] = __floats2half2_rn(pp[u].x, pp[u].y);
+                half_copy[2 * i + 1] = __floats2half2_rn(pp[u].z, pp[u].w);
+            }
         }
     }
 }
@@ -881,7 +910,7 @@ cudaError_t launch_adam(int64_t n, float* p, float* g, float* m, float* v, float
                         __half* half_copy, int64_t n_half, cudaStream_t st) {
     const int64_t n4 = n / 4;
     int grid = (int)((n4 + 255) / 256);
-    const int cap = sm_count() * 8;
+    const int cap = sm_count() * 16;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
     k_adam<<<grid, 256, 0, st>>>(n4, reinterpret_cast<float4*>(p), reinterpret_cast<float4*>(g),

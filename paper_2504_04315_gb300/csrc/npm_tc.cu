@@ -206,7 +206,10 @@ __device__ __forceinline__ float2 load_feat2(const float* g, uint32_t idx) {
 __device__ __forceinline__ float load_feat(const __half* e, int f) { return __half2float(e[f]); }
 __device__ __forceinline__ float load_feat(const float* e, int f) { return __ldg(e + f); }
 
-template <typename GT>
+// F2: the grid has 2 features per level (compile-time), so two levels' 16
+// corner loads can be in flight before blending; other grids take the
+// generic per-level path (fewer registers).
+template <bool F2, typename GT>
 __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict__ grid_h,
                                           int64_t j, bool valid, int64_t ld,
                                           const float* __restrict__ pos,
@@ -221,10 +224,36 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
         z = pos[2 * ld + j];
     }
     const int F = cfg.feat;
-    for (int l = 0; l < cfg.n_levels; ++l) {
+    int l = 0;
+    if constexpr (F2) {
+        for (; l + 1 < cfg.n_levels; l += 2) {
+            const Cell c0 = make_cell(x, y, z, cfg.level_res[l]);
+            const Cell c1 = make_cell(x, y, z, cfg.level_res[l + 1]);
+            const GT* g0 = grid_h + (size_t)cfg.level_off[l] * 2;
+            const GT* g1 = grid_h + (size_t)cfg.level_off[l + 1] * 2;
+            float2 v0[8], v1[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                v0[c] = load_feat2(g0, corner_index(cfg, l, c0, c));
+                v1[c] = load_feat2(g1, corner_index(cfg, l + 1, c1, c));
+            }
+            float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float w0 = corner_weight(c0, c), w1 = corner_weight(c1, c);
+                a0 = fmaf(w0, v0[c].x, a0);
+                a1 = fmaf(w0, v0[c].y, a1);
+                b0 = fmaf(w1, v1[c].x, b0);
+                b1 = fmaf(w1, v1[c].y, b1);
+            }
+            store_pair(sA, tile_off(row, 2 * l, kp), a0, a1, lo);
+            store_pair(sA, tile_off(row, 2 * l + 2, kp), b0, b1, lo);
+        }
+    }
+    for (; l < cfg.n_levels; ++l) {
         const Cell cl = make_cell(x, y, z, cfg.level_res[l]);
         const GT* gl = grid_h + (size_t)cfg.level_off[l] * F;
-        if (F == 2) {
+        if (F2 || F == 2) {
             float s0 = 0.0f, s1 = 0.0f;
             float2 v[8];
 #pragma unroll
@@ -374,7 +403,7 @@ __device__ __forceinline__ void tc_decode(const TcCfg& tc, const float (&raw)[4 
 
 // --------------------------------------------------------------- kernel
 
-template <int KMAX>
+template <int KMAX, bool F2>
 __global__ void __launch_bounds__(kThreads) k_forward_tc(const __grid_constant__ TcCfg tc,
                                                          const __half* __restrict__ grid_h,
                                                          const uint8_t* __restrict__ wblob,
@@ -440,7 +469,7 @@ __global__ void __launch_bounds__(kThreads) k_forward_tc(const __grid_constant__
         const int64_t ld = S.ld;
         const int64_t j = (tile - S.tile0) * kTile + t;
         const bool valid = j < n;
-        tc_encode(tc, grid_h, j, valid, ld, S.pos, S.aux, sA, t);
+        tc_encode<F2>(tc, grid_h, j, valid, ld, S.pos, S.aux, sA, t);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -623,7 +652,7 @@ __device__ __forceinline__ void store16_plain(uint8_t* base, int t, int c0, int 
     *reinterpret_cast<uint4*>(base + tile_off(t, c0 + 8, kp)) = make_uint4(h[4], h[5], h[6], h[7]);
 }
 
-template <int KMAX>
+template <int KMAX, bool F2>
 __global__ void __launch_bounds__(kThreads, 1) k_train_tc(
     const __grid_constant__ TcCfg tc, const __grid_constant__ TcTrain tt, const float* __restrict__ grid32,
     const uint8_t* __restrict__ wblob, int64_t n, int64_t ld, const float* __restrict__ pos,
@@ -675,7 +704,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_train_tc(
     for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
         const int64_t j = tile * kTile + t;
         const bool valid = j < n;
-        tc_encode(tc, grid32, j, valid, ld, pos, aux, smem + tt.h_off[0], t);
+        tc_encode<F2>(tc, grid32, j, valid, ld, pos, aux, smem + tt.h_off[0], t);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -1005,10 +1034,10 @@ cudaError_t tc_refresh_weights(npm_handle* h, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int KMAX>
+template <int KMAX, bool F2>
 static cudaError_t launch_tc(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStream_t st) {
     TcState* s = h->tc;
-    auto kern = k_forward_tc<KMAX>;
+    auto kern = k_forward_tc<KMAX, F2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem);
     if (e != cudaSuccess) return e;
     // CTAs per SM from registers and tensor memory; then carve out just the
@@ -1046,12 +1075,12 @@ static cudaError_t launch_tc(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaS
     return cudaGetLastError();
 }
 
-template <int KMAX>
+template <int KMAX, bool F2>
 static cudaError_t launch_train_tc(npm_handle* h, int64_t n, int64_t ld, const float* pos, const float* aux,
                                    const float* dir, const float* rad, const float* spdf, const float* dlogv,
                                    float* loss, cudaStream_t st) {
     TcState* s = h->tc;
-    auto kern = k_train_tc<KMAX>;
+    auto kern = k_train_tc<KMAX, F2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->train.smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -1074,16 +1103,23 @@ bool tc_can_train(npm_handle* h) { return h->tc && h->tc->can_train; }
 cudaError_t tc_train(npm_handle* h, int64_t n, int64_t ld, const float* pos, const float* aux, const float* dir,
                      const float* rad, const float* spdf, const float* dlogv, float* loss, cudaStream_t st) {
     const int K = h->cfg.K;
-    if (K <= 4) return launch_train_tc<4>(h, n, ld, pos, aux, dir, rad, spdf, dlogv, loss, st);
-    if (K <= 8) return launch_train_tc<8>(h, n, ld, pos, aux, dir, rad, spdf, dlogv, loss, st);
-    return launch_train_tc<16>(h, n, ld, pos, aux, dir, rad, spdf, dlogv, loss, st);
+    const bool f2 = h->cfg.feat_per_level == 2;
+    if (K <= 4)
+        return f2 ? launch_train_tc<4, true>(h, n, ld, pos, aux, dir, rad, spdf, dlogv, loss, st)
+                  : launch_train_tc<4, false>(h, n, ld, pos, aux, dir, rad, spdf, dlogv, loss, st);
+    if (K <= 8)
+        return f2 ? launch_train_tc<8, true>(h, n, ld, pos, aux, dir, rad, spdf, dlogv, loss, st)
+                  : launch_train_tc<8, false>(h, n, ld, pos, aux, dir, rad, spdf, dlogv, loss, st);
+    return f2 ? launch_train_tc<16, true>(h, n, ld, pos, aux, dir, rad, spdf, dlogv, loss, st)
+              : launch_train_tc<16, false>(h, n, ld, pos, aux, dir, rad, spdf, dlogv, loss, st);
 }
 
 cudaError_t tc_query_batch(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStream_t st) {
     const int K = h->cfg.K;
-    if (K <= 4) return launch_tc<4>(h, qb, max_n, st);
-    if (K <= 8) return launch_tc<8>(h, qb, max_n, st);
-    return launch_tc<16>(h, qb, max_n, st);
+    const bool f2 = h->cfg.feat_per_level == 2;
+    if (K <= 4) return f2 ? launch_tc<4, true>(h, qb, max_n, st) : launch_tc<4, false>(h, qb, max_n, st);
+    if (K <= 8) return f2 ? launch_tc<8, true>(h, qb, max_n, st) : launch_tc<8, false>(h, qb, max_n, st);
+    return f2 ? launch_tc<16, true>(h, qb, max_n, st) : launch_tc<16, false>(h, qb, max_n, st);
 }
 
 npm_status tc_query(npm_handle* h, int64_t n, int64_t ld, const float* pos, const float* aux,
