@@ -105,6 +105,18 @@ def dist_env():
     return rank, world, local
 
 
+def job_throughput(local_ms: float, units_per_rank: int, steps: int, world: int, dist=None,
+                   device: str = "cpu"):
+    """Whole-job throughput: the slowest rank's time (max over ranks) for
+    units_per_rank * steps units on every rank. Returns (max_ms, units/s)."""
+    import torch
+    t = torch.tensor([float(local_ms)], device=device, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    return max_ms, units_per_rank * steps * world / (max_ms / 1e3)
+
+
 def workload_of(name):
     return synth.WORKLOADS[name]
 
@@ -248,12 +260,7 @@ def main():
     if dist:
         dist.barrier()
     per = [evs[i].elapsed_time(evs[i + 1]) for i in range(K)]
-    total_ms = evs[0].elapsed_time(evs[K])
-    t = torch.tensor([total_ms], device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = n * K * world / (total_ms / 1e3)
+    total_ms, value = job_throughput(evs[0].elapsed_time(evs[K]), n, K, world, dist, "cuda")
     kern_ms = statistics.mean(per)
 
     # End to end through the host-buffer entry point: pinned inputs copied
