@@ -26,7 +26,17 @@ constexpr int kTQ = 64;   // queries per tile
 constexpr int kNT = 128;  // threads per CTA
 constexpr unsigned kFull = 0xffffffffu;
 
+// Activation row stride (floats) of the forward kernel instance whose
+// widest layer is 16 * I: the padding of 4 keeps the 16 rows a warp reads
+// in distinct banks.
+__host__ __device__ constexpr int fwd_act_stride(int I) { return 16 * I + 4; }
+
 // ----------------------------------------------------------- tile GEMM
+
+// Named barrier of tile group `group` (kNT threads; barrier 0 is the CTA's).
+__device__ __forceinline__ void group_sync(int group) {
+    asm volatile("bar.sync %0, %1;" ::"r"(group + 1), "r"(kNT) : "memory");
+}
 
 template <int NI>
 __device__ __forceinline__ void load_w(const float* p, float (&w)[NI]) {
@@ -51,11 +61,16 @@ __device__ __forceinline__ void load_w(const float* p, float (&w)[NI]) {
 // out[q][n] = f(sum_k in[q][k] * WT[k][n]) for q < 64, n < N. WT rows are
 // padded to NP = 16 * NI columns (zeros beyond N). mode 0: identity,
 // 1: ReLU, 2: keep where mask[q][n] > 0 (ReLU derivative), else 0.
-template <int NI>
-__device__ __forceinline__ void tile_gemm(int t, const float* __restrict__ in, int AS, int K,
-                                          const float* __restrict__ WT, int NP,
-                                          float* __restrict__ out, int N, int mode,
-                                          const float* __restrict__ mask) {
+// AST > 0: the activation row stride is the compile-time AST (so row and
+// weight addresses are immediate offsets of two pointers); else AS_rt.
+// INPLACE: out may equal in; the tile group (named barrier group + 1)
+// synchronises between the last read of in and the first store.
+template <int NI, int AST, bool INPLACE>
+__device__ __forceinline__ void tile_gemm(int t, const float* in, int AS_rt, int K,
+                                          const float* __restrict__ WT, float* out, int N, int mode,
+                                          const float* __restrict__ mask, int group) {
+    const int AS = AST > 0 ? AST : AS_rt;
+    constexpr int NP = 16 * NI;
     const int g = t & 15, qg = t >> 4;
     // Accumulators paired along adjacent outputs: one packed two-lane FMA
     // (fma.rn on each lane, the same rounding as fmaf) per pair.
@@ -90,31 +105,45 @@ __device__ __forceinline__ void tile_gemm(int t, const float* __restrict__ in, i
             }
         }
     }
+    if constexpr (INPLACE) group_sync(group);
+    const bool full = g * NI + NI <= N;  // all NI outputs of this thread exist
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int row = (qg + 8 * j) * AS;
+        float v[NI];
 #pragma unroll
         for (int i = 0; i < NI; ++i) {
-            const int n = g * NI + i;
-            if (n < N) {
-                float v = NI == 1 ? acc1[j] : ((i & 1) ? acc[j][i >> 1].y : acc[j][i >> 1].x);
-                if (mode == 1) v = fmaxf(v, 0.0f);
-                if (mode == 2) v = mask[row + n] > 0.0f ? v : 0.0f;
-                out[row + n] = v;
+            v[i] = NI == 1 ? acc1[j] : ((i & 1) ? acc[j][i >> 1].y : acc[j][i >> 1].x);
+            if (mode == 1) v[i] = fmaxf(v[i], 0.0f);
+            if (mode == 2) v[i] = (g * NI + i < N && mask[row + g * NI + i] > 0.0f) ? v[i] : 0.0f;
+        }
+        if constexpr (NI % 4 == 0) {
+            if (full) {
+#pragma unroll
+                for (int i = 0; i < NI; i += 4)
+                    *reinterpret_cast<float4*>(out + row + g * NI + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                continue;
             }
         }
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+            if (g * NI + i < N) out[row + g * NI + i] = v[i];
     }
 }
 
 // One layer for the tile; only the register tiles up to NIMAX outputs per
-// thread are instantiated (NP <= 16 * NIMAX is guaranteed by the launcher).
-template <int NIMAX>
+// thread are instantiated (NP = 16 NI <= 16 * NIMAX is guaranteed by the
+// launcher). AST as in tile_gemm.
+template <int NIMAX, int AST = 0, bool INPLACE = false>
 __device__ __forceinline__ void layer(int t, const float* in, int AS, int K, const float* WT, int NP,
-                                      float* out, int N, int mode, const float* mask) {
-    if (NP == 16) tile_gemm<1>(t, in, AS, K, WT, NP, out, N, mode, mask);
-    else if (NIMAX >= 2 && NP == 32) tile_gemm<(NIMAX >= 2 ? 2 : 1)>(t, in, AS, K, WT, NP, out, N, mode, mask);
-    else if (NIMAX >= 4 && NP == 64) tile_gemm<(NIMAX >= 4 ? 4 : 1)>(t, in, AS, K, WT, NP, out, N, mode, mask);
-    else if (NIMAX >= 8) tile_gemm<(NIMAX >= 8 ? 8 : 1)>(t, in, AS, K, WT, NP, out, N, mode, mask);
+                                      float* out, int N, int mode, const float* mask, int group = 0) {
+    if (NP == 16) tile_gemm<1, AST, INPLACE>(t, in, AS, K, WT, out, N, mode, mask, group);
+    else if (NIMAX >= 2 && NP == 32)
+        tile_gemm<(NIMAX >= 2 ? 2 : 1), AST, INPLACE>(t, in, AS, K, WT, out, N, mode, mask, group);
+    else if (NIMAX >= 4 && NP == 64)
+        tile_gemm<(NIMAX >= 4 ? 4 : 1), AST, INPLACE>(t, in, AS, K, WT, out, N, mode, mask, group);
+    else if (NIMAX >= 8)
+        tile_gemm<(NIMAX >= 8 ? 8 : 1), AST, INPLACE>(t, in, AS, K, WT, out, N, mode, mask, group);
 }
 
 // ------------------------------------------------------------- encode
@@ -396,10 +425,6 @@ __device__ __forceinline__ void epilogue_tile(int t, const DevCfg& cfg, const fl
 
 // ------------------------------------------------------ forward kernel
 
-__device__ __forceinline__ void group_sync(int group) {
-    asm volatile("bar.sync %0, %1;" ::"r"(group + 1), "r"(kNT) : "memory");
-}
-
 // One CTA per SM holds G tile groups of 128 threads. The groups share one
 // copy of the weights in shared memory and each walks its own 64-query tiles
 // with its own activation buffers and named barrier.
@@ -410,12 +435,11 @@ __global__ void __launch_bounds__(512, 1) k_forward_fp32(const __grid_constant__
                                                          const __grid_constant__ QueryBatch qb) {
     extern __shared__ float4 smem4[];
     float* sW = reinterpret_cast<float*>(smem4);
-    const int AS = cfg.max_width + 4;
+    constexpr int AS = fwd_act_stride(NIMAX);
     const int G = blockDim.x / kNT;
     const int group = threadIdx.x / kNT;
     const int t = threadIdx.x % kNT;
-    float* actA = sW + cfg.fwd_floats + group * 2 * kTQ * AS;
-    float* actB = actA + kTQ * AS;
+    float* act = sW + cfg.fwd_floats + group * kTQ * AS;  // one tile, layers in place
     for (int i = threadIdx.x; i < cfg.fwd_floats / 4; i += blockDim.x)
         smem4[i] = __ldg(reinterpret_cast<const float4*>(wfwd) + i);
     __syncthreads();
@@ -430,20 +454,15 @@ __global__ void __launch_bounds__(512, 1) k_forward_fp32(const __grid_constant__
         const QuerySeg& S = qb.seg[s];
         const int64_t n = (s == 0 && qb.n_dev) ? n0 : S.n;
         const int64_t base = (tile - S.tile0) * kTQ;
-        encode_tile(t, cfg, grid, base, n, S.ld, S.pos, S.aux, actA, AS);
+        encode_tile(t, cfg, grid, base, n, S.ld, S.pos, S.aux, act, AS);
         group_sync(group);
-        float* in = actA;
-        float* out = actB;
         for (int l = 0; l < cfg.n_layers; ++l) {
             const bool last = l == cfg.n_layers - 1;
-            layer<NIMAX>(t, in, AS, cfg.widths[l], sW + cfg.off_fwd[l], cfg.np_fwd[l], out,
-                         cfg.widths[l + 1], last ? 0 : 1, nullptr);
+            layer<NIMAX, AS, true>(t, act, AS, cfg.widths[l], sW + cfg.off_fwd[l], cfg.np_fwd[l], act,
+                                   cfg.widths[l + 1], last ? 0 : 1, nullptr, group);
             group_sync(group);
-            float* tmp = in;
-            in = out;
-            out = tmp;
         }
-        epilogue_tile<SAMPLE, KH>(t, cfg, in, AS, base, n, S.ld, S.uin, S.ufrac, S.dir, S.pdf, S.mix);
+        epilogue_tile<SAMPLE, KH>(t, cfg, act, AS, base, n, S.ld, S.uin, S.ufrac, S.dir, S.pdf, S.mix);
         group_sync(group);
     }
 }
@@ -770,9 +789,6 @@ __global__ void k_copy_loss(const float* __restrict__ acc, float* __restrict__ o
 
 // ----------------------------------------------------------- launchers
 
-size_t fwd_smem_bytes(const DevCfg& c) {
-    return sizeof(float) * ((size_t)c.fwd_floats + 2 * (size_t)kTQ * (c.max_width + 4));
-}
 
 size_t train_smem_bytes(const DevCfg& c) {
     return sizeof(float) *
@@ -811,9 +827,17 @@ int carveout_percent(size_t bytes) {
 static int fp32_instance(const DevCfg& cfg) {
     int need = 1;
     for (int l = 0; l < cfg.n_layers; ++l) need = cfg.np_fwd[l] / 16 > need ? cfg.np_fwd[l] / 16 : need;
+    // the activation rows (stride fwd_act_stride(I)) hold every width
+    const int mw = (cfg.max_width + 15) / 16;
+    need = mw > need ? mw : need;
     const int kh = (cfg.K + 1) / 2;
     need = kh > need ? kh : need;
     return need <= 2 ? 2 : need <= 4 ? 4 : 8;
+}
+
+// Shared memory of a one-group CTA: weights and one activation tile.
+size_t fwd_smem_bytes(const DevCfg& c) {
+    return sizeof(float) * ((size_t)c.fwd_floats + (size_t)kTQ * fwd_act_stride(fp32_instance(c)));
 }
 
 template <bool SAMPLE, int I>
@@ -821,7 +845,7 @@ static cudaError_t launch_fwd_inst(const DevCfg& cfg, const float* grid, const f
                                    const QueryBatch& qb, int64_t tiles_hint, cudaStream_t st) {
     auto kern = k_forward_fp32<SAMPLE, I, I>;
     const size_t wbytes = sizeof(float) * (size_t)cfg.fwd_floats;
-    const size_t gbytes = sizeof(float) * 2 * (size_t)kTQ * (cfg.max_width + 4);
+    const size_t gbytes = sizeof(float) * (size_t)kTQ * fwd_act_stride(I);
     int G = (int)((227 * 1024 - wbytes) / gbytes);
     if (G > 4) G = 4;
     // Tuning override (groups per CTA) for launch-configuration sweeps.

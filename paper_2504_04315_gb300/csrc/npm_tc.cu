@@ -48,6 +48,9 @@ struct TcCfg {
     uint32_t w_bytes;  // bytes of one weight blob (multiple of 128); the
                        // residual (lo) blob follows when split
     uint32_t a_bytes;  // bytes of one activation tile; the lo tile follows
+    uint32_t a0_bytes; // bytes of the layer-0 input tile when it has its own
+                       // buffer (the encoding leaves all-zero 8-column chunks);
+                       // 0 when layer 0 shares the buffer of layers >= 1
     int split;         // 1: BF16 residual operands (three MMAs per K step)
     uint32_t tmem_cols;
     int enc_width;     // meaningful network inputs
@@ -203,30 +206,48 @@ __device__ __forceinline__ float2 load_feat2(const __half* g, uint32_t idx) {
 __device__ __forceinline__ float2 load_feat2(const float* g, uint32_t idx) {
     return __ldg(reinterpret_cast<const float2*>(g) + idx);
 }
+// Features 4h .. 4h+3 of entry idx of a table with F = 4 or 8 features: the
+// raw 8-byte FP16 or 16-byte FP32 vector, widened to float4 at use.
+__device__ __forceinline__ uint2 load_raw4(const __half* g, uint32_t idx, int F, int h) {
+    return __ldg(reinterpret_cast<const uint2*>(g) + (size_t)idx * (F >> 2) + h);
+}
+__device__ __forceinline__ float4 load_raw4(const float* g, uint32_t idx, int F, int h) {
+    return __ldg(reinterpret_cast<const float4*>(g) + (size_t)idx * (F >> 2) + h);
+}
+__device__ __forceinline__ float4 widen4(uint2 raw) {
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&raw.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float4 widen4(float4 v) { return v; }
 __device__ __forceinline__ float load_feat(const __half* e, int f) { return __half2float(e[f]); }
 __device__ __forceinline__ float load_feat(const float* e, int f) { return __ldg(e + f); }
 
 // F2: the grid has 2 features per level (compile-time), so two levels' 16
 // corner loads can be in flight before blending; other grids take the
 // generic per-level path (fewer registers).
+// Levels [lbeg, lend) are encoded; tail: also the product-mode inputs and
+// the zero padding. lo: byte offset of the residual tile (0 without split).
+// pad_all: write zeros up to kp; otherwise only up to the next 8-column
+// chunk (the caller keeps the all-zero chunks beyond it written).
 template <bool F2, typename GT>
 __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict__ grid_h,
                                           int64_t j, bool valid, int64_t ld,
                                           const float* __restrict__ pos,
-                                          const float* __restrict__ aux, uint8_t* sA, int row) {
+                                          const float* __restrict__ aux, uint8_t* sA, int row,
+                                          uint32_t lo, bool pad_all, int lbeg, int lend, bool tail) {
     const DevCfg& cfg = tc.base;
     const int kp = tc.layer[0].Kp;
-    const uint32_t lo = tc.split ? tc.a_bytes : 0u;
     float x = 0.0f, y = 0.0f, z = 0.0f;
     if (valid) {
         x = pos[j];
         y = pos[ld + j];
         z = pos[2 * ld + j];
     }
-    const int F = cfg.feat;
-    int l = 0;
+    const int F = F2 ? 2 : cfg.feat;
+    int l = lbeg;
     if constexpr (F2) {
-        for (; l + 1 < cfg.n_levels; l += 2) {
+        for (; l + 1 < lend; l += 2) {
             const Cell c0 = make_cell(x, y, z, cfg.level_res[l]);
             const Cell c1 = make_cell(x, y, z, cfg.level_res[l + 1]);
             const GT* g0 = grid_h + (size_t)cfg.level_off[l] * 2;
@@ -250,7 +271,7 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
             store_pair(sA, tile_off(row, 2 * l + 2, kp), b0, b1, lo);
         }
     }
-    for (; l < cfg.n_levels; ++l) {
+    for (; l < lend; ++l) {
         const Cell cl = make_cell(x, y, z, cfg.level_res[l]);
         const GT* gl = grid_h + (size_t)cfg.level_off[l] * F;
         if (F2 || F == 2) {
@@ -265,29 +286,39 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
                 s1 = fmaf(w, v[c].y, s1);
             }
             store_pair(sA, tile_off(row, 2 * l, kp), s0, s1, lo);
-        } else {
-            float s[8];
+        } else if (F == 4 || F == 8) {
+            // One vector load per corner and group of 4 features.
+            uint32_t idx[8];
 #pragma unroll
-            for (int f = 0; f < 8; ++f) s[f] = 0.0f;
+            for (int c = 0; c < 8; ++c) idx[c] = corner_index(cfg, l, cl, c);
+            for (int h = 0; h < (F >> 2); ++h) {
+                decltype(load_raw4(gl, 0u, F, 0)) raw[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const float w = corner_weight(cl, c);
-                const GT* e = gl + (size_t)corner_index(cfg, l, cl, c) * F;
+                for (int c = 0; c < 8; ++c) raw[c] = load_raw4(gl, idx[c], F, h);
+                float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
-                for (int f = 0; f < 8; ++f)
-                    if (f < F) s[f] = fmaf(w, load_feat(e, f), s[f]);
-            }
-#pragma unroll
-            for (int f = 0; f < 8; f += 2)
-                if (f < F) {
-                    const int k = l * F + f;
-                    if (f + 1 < F)
-                        store_pair(sA, tile_off(row, k, kp), s[f], s[f + 1], lo);
-                    else
-                        store_one(sA, tile_off(row, k, kp), s[f], lo);
+                for (int c = 0; c < 8; ++c) {
+                    const float w = corner_weight(cl, c);
+                    const float4 v = widen4(raw[c]);
+                    acc.x = fmaf(w, v.x, acc.x);
+                    acc.y = fmaf(w, v.y, acc.y);
+                    acc.z = fmaf(w, v.z, acc.z);
+                    acc.w = fmaf(w, v.w, acc.w);
                 }
+                const int k = l * F + 4 * h;
+                store_pair(sA, tile_off(row, k, kp), acc.x, acc.y, lo);
+                store_pair(sA, tile_off(row, k + 2, kp), acc.z, acc.w, lo);
+            }
+        } else {
+            // F = 1
+            float s = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                s = fmaf(corner_weight(cl, c), load_feat(gl + corner_index(cfg, l, cl, c), 0), s);
+            store_one(sA, tile_off(row, l, kp), s, lo);
         }
     }
+    if (!tail) return;
     int k = cfg.grid_feats;
     if (cfg.mode == NPM_PRODUCT) {
         float e[21];
@@ -308,7 +339,8 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
         for (int i = 0; i < 21; ++i) store_one(sA, tile_off(row, k + i, kp), e[i], lo);
         k += 21;
     }
-    for (; k < kp; ++k) store_one(sA, tile_off(row, k, kp), 0.0f, lo);
+    const int kend = pad_all ? kp : min(kp, (k + 7) & ~7);
+    for (; k < kend; ++k) store_one(sA, tile_off(row, k, kp), 0.0f, lo);
 }
 
 // --------------------------------------------------------------- decode
@@ -412,7 +444,9 @@ __global__ void __launch_bounds__(kThreads) k_forward_tc(const __grid_constant__
     extern __shared__ __align__(1024) uint8_t smem[];
     const int nsplit = tc.split ? 2 : 1;
     uint8_t* sW = smem;
-    uint8_t* sA = smem + nsplit * tc.w_bytes;
+    uint8_t* sA = smem + nsplit * (tc.w_bytes + tc.a0_bytes);  // inputs of layers >= 1
+    uint8_t* sA0 = tc.a0_bytes ? smem + nsplit * tc.w_bytes : sA;  // layer-0 input (encoding)
+    const uint32_t a0_lo = tc.a0_bytes ? tc.a0_bytes : tc.a_bytes;  // its residual tile
     uint64_t* bars = reinterpret_cast<uint64_t*>(sA + nsplit * tc.a_bytes);  // [0] mma, [1] weights
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
     const int t = threadIdx.x;
@@ -449,9 +483,19 @@ __global__ void __launch_bounds__(kThreads) k_forward_tc(const __grid_constant__
             "l"(wblob), "r"(wb), "r"(bar_w)
             : "memory");
     }
+    // The all-zero 8-column chunks of the encoding are written once: the
+    // layer-0 buffer holds nothing else.
+    if (tc.a0_bytes) {
+        const int kp0 = tc.layer[0].Kp;
+        for (int c = (tc.enc_width + 7) >> 3; c < (kp0 >> 3); ++c) {
+            *reinterpret_cast<uint4*>(sA0 + tile_off(t, 8 * c, kp0)) = make_uint4(0u, 0u, 0u, 0u);
+            if (tc.split)
+                *reinterpret_cast<uint4*>(sA0 + a0_lo + tile_off(t, 8 * c, kp0)) = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
     bool ok = !__syncthreads_or(!mbar_wait_bounded(bar_w, 0));
     uint32_t phase = 0;
-    const uint32_t sA_addr = smem_u32(sA);
+    const uint32_t sA_addr = smem_u32(sA), sA0_addr = smem_u32(sA0);
     const uint32_t sW_addr = smem_u32(sW);
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     const int L = tc.base.n_layers;
@@ -469,7 +513,8 @@ __global__ void __launch_bounds__(kThreads) k_forward_tc(const __grid_constant__
         const int64_t ld = S.ld;
         const int64_t j = (tile - S.tile0) * kTile + t;
         const bool valid = j < n;
-        tc_encode<F2>(tc, grid_h, j, valid, ld, S.pos, S.aux, sA, t);
+        tc_encode<F2>(tc, grid_h, j, valid, ld, S.pos, S.aux, sA0, t, tc.split ? a0_lo : 0u, false, 0,
+                      tc.base.n_levels, true);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -479,14 +524,16 @@ __global__ void __launch_bounds__(kThreads) k_forward_tc(const __grid_constant__
             if (t == 0) {
                 tc_fence_after();
                 const uint32_t sbo = (uint32_t)(ly.Kp >> 3) * 128u;
+                const uint32_t a_addr = l == 0 ? sA0_addr : sA_addr;
+                const uint32_t a_lo = l == 0 ? a0_lo : tc.a_bytes;
                 for (int s = 0; s < (ly.Kp >> 4); ++s) {
-                    const uint64_t ad = umma_desc(sA_addr + s * 256u, 128u, sbo);
+                    const uint64_t ad = umma_desc(a_addr + s * 256u, 128u, sbo);
                     const uint64_t bd = umma_desc(sW_addr + ly.w_off + s * 256u, 128u, sbo);
                     mma_bf16(tmem, ad, bd, ly.idesc, s > 0 ? 1u : 0u);
                     if (tc.split) {
                         // hi*lo and lo*hi residual products
                         const uint64_t bdl = umma_desc(sW_addr + tc.w_bytes + ly.w_off + s * 256u, 128u, sbo);
-                        const uint64_t adl = umma_desc(sA_addr + tc.a_bytes + s * 256u, 128u, sbo);
+                        const uint64_t adl = umma_desc(a_addr + a_lo + s * 256u, 128u, sbo);
                         mma_bf16(tmem, ad, bdl, ly.idesc, 1u);
                         mma_bf16(tmem, adl, bd, ly.idesc, 1u);
                     }
@@ -574,97 +621,169 @@ struct TcTrain {
     uint32_t dw_col[NPM_MAX_LAYERS];
     uint32_t idesc_dw[NPM_MAX_LAYERS];  // A MN-major, B MN-major, N = Kp_l
     uint32_t idesc_dx[NPM_MAX_LAYERS];  // A K-major,  B MN-major, N = Kp_l
-    uint32_t d_off, bar_off, smem, tmem_cols;
+    uint32_t d_off, x_off, bar_off, smem, tmem_cols;
     int64_t woff[NPM_MAX_LAYERS];       // packed offset of W_l in the MLP region
     int split;                          // BF16 residual operands (three MMAs per K step)
     uint32_t hlo_off;                   // residual of the current layer's input tile
     uint32_t dlo_off;                   // residual of the delta tile
 };
 
-// d log V / d raw for one query (all K lobes in this thread), in the log
-// domain; returns s * log V and writes s * d log V / d raw to d[].
+// Training runs two threads per sample row: thread t serves row t & 127 and
+// half t >> 7 of the row's work (grid levels, epilogue column chunks,
+// lobes). Warps w and w + 4 read the same TMEM lane quarter.
+constexpr int kTrainThreads = 2 * kTile;
+
+// Half h of the lobes of one sample, lobes i = h KMAX/2 + q. Pass 1 forms
+// each lobe's terms and the half's partial log-sum-exps of the softmax
+// logits (m1, s1) and of the unnormalised log lobe values
+// a'_i = raw_i + log c(kappa_i) + kappa_i (mu_i.w - 1) (m2, s2); the caller
+// combines both halves' partials (log V = LSE(a') - LSE(raw)).
 template <int KMAX>
-__device__ __forceinline__ float tc_grad_raw(const DevCfg& cfg, const float (&raw)[4 * KMAX], const float w[3],
-                                             float s, float (&d)[4 * KMAX]) {
-    const int K = cfg.K;
-    float mx = -INFINITY;
+struct GradHalf {
+    static constexpr int KH = KMAX / 2;
+    float r0[KH], ap[KH], kap[KH], md[KH], wdt[KH], wdp[KH], sk[KH], st[KH], sp[KH];
+    bool act[KH];
+
+    __device__ __forceinline__ float4 pass1(const DevCfg& cfg, int h, const float (&raw)[4 * KH], const float w[3]) {
+        float m1 = -INFINITY, m2 = -INFINITY;
 #pragma unroll
-    for (int i = 0; i < KMAX; ++i)
-        if (i < K) mx = fmaxf(mx, raw[4 * i]);
-    float ssum = 0.0f;
-#pragma unroll
-    for (int i = 0; i < KMAX; ++i)
-        if (i < K) ssum += expf(raw[4 * i] - mx);
-    const float lse = mx + logf(ssum);
-    float a[KMAX], kap[KMAX], md[KMAX], wdt[KMAX], wdp[KMAX], sk[KMAX], st[KMAX], sp[KMAX], lp[KMAX];
-    float amax = -INFINITY;
-#pragma unroll
-    for (int i = 0; i < KMAX; ++i)
-        if (i < K) {
-            lp[i] = raw[4 * i] - lse;
-            const float rk = raw[4 * i + 1];
+        for (int q = 0; q < KH; ++q) {
+            act[q] = h * KH + q < cfg.K;
+            r0[q] = raw[4 * q];
+            const float rk = raw[4 * q + 1];
             if (cfg.kappa_act == NPM_EXP) {
-                kap[i] = expf(rk);
-                sk[i] = kap[i];
+                kap[q] = __expf(rk);
+                sk[q] = kap[q];
             } else {
-                kap[i] = softplus(rk);
-                sk[i] = logistic(rk);
+                // softplus and its derivative, the logistic, from one e^{-|rk|}
+                const float e = __expf(-fabsf(rk));
+                const float r1 = __fdividef(1.0f, 1.0f + e);
+                kap[q] = fmaxf(rk, 0.0f) + __logf(1.0f + e);
+                sk[q] = rk >= 0.0f ? r1 : e * r1;
             }
-            st[i] = logistic(raw[4 * i + 2]);
-            sp[i] = logistic(raw[4 * i + 3]);
+            st[q] = logistic_fast(raw[4 * q + 2]);
+            sp[q] = logistic_fast(raw[4 * q + 3]);
+            // theta = pi st, phi = pi + pi (2 sp - 1): sine/cosine on [-pi, pi]
             float sth, cth, sph, cph;
-            sincosf(kPi * st[i], &sth, &cth);
-            sincosf(2.0f * kPi * sp[i], &sph, &cph);
-            md[i] = sth * cph * w[0] + sth * sph * w[1] + cth * w[2];
-            wdt[i] = cth * cph * w[0] + cth * sph * w[1] - sth * w[2];
-            wdp[i] = -sth * sph * w[0] + sth * cph * w[1];
-            a[i] = lp[i] + logf(vmf_scaled_norm(kap[i])) + kap[i] * (md[i] - 1.0f);
-            amax = fmaxf(amax, a[i]);
+            __sincosf(kPi * st[q] - 0.5f * kPi, &cth, &sth);
+            cth = -cth;
+            __sincosf(kPi * (2.0f * sp[q] - 1.0f), &sph, &cph);
+            sph = -sph;
+            cph = -cph;
+            md[q] = sth * cph * w[0] + sth * sph * w[1] + cth * w[2];
+            wdt[q] = cth * cph * w[0] + cth * sph * w[1] - sth * w[2];
+            wdp[q] = -sth * sph * w[0] + sth * cph * w[1];
+            ap[q] = r0[q] + __logf(vmf_scaled_norm_fast(kap[q])) + kap[q] * (md[q] - 1.0f);
+            if (act[q]) {
+                m1 = fmaxf(m1, r0[q]);
+                m2 = fmaxf(m2, ap[q]);
+            }
         }
-    float es = 0.0f;
+        float s1 = 0.0f, s2 = 0.0f;
 #pragma unroll
-    for (int i = 0; i < KMAX; ++i)
-        if (i < K) es += expf(a[i] - amax);
-    const float logV = amax + logf(es);
+        for (int q = 0; q < KH; ++q)
+            if (act[q]) {
+                s1 += __expf(r0[q] - m1);
+                s2 += __expf(ap[q] - m2);
+            }
+        return make_float4(m1, s1, m2, s2);
+    }
+
+    // s d log V / d raw of this half's lobes (zero for lobes beyond K).
+    __device__ __forceinline__ void pass2(float lse, float lsa, float s, float (&d)[4 * KH]) const {
 #pragma unroll
-    for (int i = 0; i < KMAX; ++i) {
-        if (i < K) {
-            const float r = expf(a[i] - logV);
-            const float lam = expf(lp[i]);
-            const float sr = s * r;
-            d[4 * i + 0] = s * (r - lam);
-            d[4 * i + 1] = sr * (inv_minus_coth(kap[i]) + md[i]) * sk[i];
-            d[4 * i + 2] = sr * kap[i] * wdt[i] * kPi * st[i] * (1.0f - st[i]);
-            d[4 * i + 3] = sr * kap[i] * wdp[i] * 2.0f * kPi * sp[i] * (1.0f - sp[i]);
-        } else {
-            d[4 * i + 0] = d[4 * i + 1] = d[4 * i + 2] = d[4 * i + 3] = 0.0f;
+        for (int q = 0; q < KH; ++q) {
+            if (act[q]) {
+                const float r = __expf(ap[q] - lsa);   // posterior of lobe q
+                const float lam = __expf(r0[q] - lse); // its mixture weight
+                const float sr = s * r;
+                d[4 * q + 0] = s * (r - lam);
+                d[4 * q + 1] = sr * (inv_minus_coth(kap[q]) + md[q]) * sk[q];
+                d[4 * q + 2] = sr * kap[q] * wdt[q] * kPi * st[q] * (1.0f - st[q]);
+                d[4 * q + 3] = sr * kap[q] * wdp[q] * 2.0f * kPi * sp[q] * (1.0f - sp[q]);
+            } else {
+                d[4 * q + 0] = d[4 * q + 1] = d[4 * q + 2] = d[4 * q + 3] = 0.0f;
+            }
         }
     }
-    return s * logV;
+};
+
+// log(e^{m_a} s_a + e^{m_b} s_b) for partial sums that may be empty (s = 0).
+__device__ __forceinline__ float lse_combine(float ma, float sa, float mb, float sb) {
+    const float m = fmaxf(ma, mb);
+    float t = 0.0f;
+    if (sa > 0.0f) t += sa * __expf(ma - m);
+    if (sb > 0.0f) t += sb * __expf(mb - m);
+    return m + __logf(t);
 }
 
-// Stores 16 values as BF16 at row t, columns c0 .. c0+15 of a K-major tile.
-__device__ __forceinline__ void store16_plain(uint8_t* base, int t, int c0, int kp, const float* v) {
-    uint32_t h[8];
+// NC (a multiple of 8) values as BF16 at row t, columns c0 .. c0+NC of a
+// K-major tile, with their residuals lo_off bytes on when lo_off != 0.
+template <int NC>
+__device__ __forceinline__ void store_cols(uint8_t* base, int t, int c0, int kp, const float* v, uint32_t lo_off) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) h[i] = pack_bf16(v[2 * i], v[2 * i + 1]);
-    *reinterpret_cast<uint4*>(base + tile_off(t, c0, kp)) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4*>(base + tile_off(t, c0 + 8, kp)) = make_uint4(h[4], h[5], h[6], h[7]);
+    for (int c = 0; c < NC; c += 8) {
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __nv_bfloat162 hb = __floats2bfloat162_rn(v[c + 2 * i], v[c + 2 * i + 1]);
+            hw[i] = *reinterpret_cast<uint32_t*>(&hb);
+            const float2 hf = __bfloat1622float2(hb);
+            lw[i] = pack_bf16(v[c + 2 * i] - hf.x, v[c + 2 * i + 1] - hf.y);
+        }
+        const uint32_t off = tile_off(t, c0 + c, kp);
+        *reinterpret_cast<uint4*>(base + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        if (lo_off) *reinterpret_cast<uint4*>(base + lo_off + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+}
+
+// Encoder-gradient scatter (Eq. 11 transposed) of levels lbeg .. lbeg+NLV
+// with FF features per level; dg holds their 16 columns.
+template <int FF, int NLV>
+__device__ __forceinline__ void scatter_levels(const DevCfg& cfg, float* __restrict__ grad, float x, float y,
+                                               float z, int lbeg, const float (&dg)[16]) {
+#pragma unroll
+    for (int q = 0; q < NLV; ++q) {
+        const int l = lbeg + q;
+        if (l < cfg.n_levels) {
+            const Cell cl = make_cell(x, y, z, cfg.level_res[l]);
+            float* gl = grad + (size_t)cfg.level_off[l] * FF;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float wc = corner_weight(cl, c);
+                float* e = gl + (size_t)corner_index(cfg, l, cl, c) * FF;
+                if constexpr (FF == 1) {
+                    atomicAdd(e, wc * dg[q]);
+                } else if constexpr (FF == 2) {
+                    atomicAdd(reinterpret_cast<float2*>(e), make_float2(wc * dg[2 * q], wc * dg[2 * q + 1]));
+                } else {
+#pragma unroll
+                    for (int f = 0; f < FF; f += 4)
+                        atomicAdd(reinterpret_cast<float4*>(e + f),
+                                  make_float4(wc * dg[FF * q + f], wc * dg[FF * q + f + 1], wc * dg[FF * q + f + 2],
+                                              wc * dg[FF * q + f + 3]));
+                }
+            }
+        }
+    }
 }
 
 template <int KMAX, bool F2>
-__global__ void __launch_bounds__(kThreads, 1) k_train_tc(
+__global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(
     const __grid_constant__ TcCfg tc, const __grid_constant__ TcTrain tt, const float* __restrict__ grid32,
     const uint8_t* __restrict__ wblob, int64_t n, int64_t ld, const float* __restrict__ pos,
     const float* __restrict__ aux, const float* __restrict__ dir, const float* __restrict__ rad,
     const float* __restrict__ spdf, const float* __restrict__ dlogv, float inv_n, float* __restrict__ grad,
     int64_t mlp_off, float* __restrict__ loss, int* __restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem[];
+    constexpr int KH = KMAX / 2;
     uint8_t* sW = smem;
     uint8_t* sD = smem + tt.d_off;
+    float4* xch = reinterpret_cast<float4*>(smem + tt.x_off);  // [2][kTile] partial log-sum-exps
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + tt.bar_off);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
     const int t = threadIdx.x, warp = t >> 5;
+    const int row = t & (kTile - 1), half = t >> 7;
     const uint32_t bar_mma = smem_u32(&bars[0]), bar_w = smem_u32(&bars[1]);
     const DevCfg& cfg = tc.base;
     const int L = cfg.n_layers;
@@ -692,23 +811,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_train_tc(
                      "l"(wblob), "r"(wbytes), "r"(bar_w)
                      : "memory");
     }
-    bool ok = !__syncthreads_or(!mbar_wait_bounded(bar_w, 0));
+    bool ok = !__syncthreads_or(warp == 0 && !mbar_wait_bounded(bar_w, 0));
     uint32_t phase = 0;
     const uint32_t sW_addr = smem_u32(sW), sD_addr = smem_u32(sD), base_addr = smem_u32(smem);
     const uint32_t wlo = tc.w_bytes;                      // residual weights follow the high parts
     const uint32_t hlo_addr = base_addr + tt.hlo_off, dlo_addr = base_addr + tt.dlo_off;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    // Grid levels of this half: [lv0, lv1); the second half also encodes the
+    // product-mode inputs and the padding.
+    const int nl0 = (cfg.n_levels + 1) / 2;
+    const int lv0 = half ? nl0 : 0, lv1 = half ? cfg.n_levels : nl0;
     float lacc = 0.0f;
     bool first = true;
     const int64_t ntiles = (n + kTile - 1) / kTile;
     for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-        const int64_t j = tile * kTile + t;
+        const int64_t j = tile * kTile + row;
         const bool valid = j < n;
-        tc_encode<F2>(tc, grid32, j, valid, ld, pos, aux, smem + tt.h_off[0], t);
+        tc_encode<F2>(tc, grid32, j, valid, ld, pos, aux, smem + tt.h_off[0], row, tc.split ? tc.a_bytes : 0u,
+                      true, lv0, lv1, half == 1);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
-        float raw[4 * KMAX];
+        float raw[4 * KH];
         // Forward, keeping every layer's input tile.
         for (int l = 0; l < L && ok; ++l) {
             const TcLayer& ly = tc.layer[l];
@@ -726,7 +850,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_train_tc(
                 }
                 mma_commit(bar_mma);
             }
-            const bool done = mbar_wait_bounded(bar_mma, phase);
+            // Warp 0 spins on the barrier; the others sleep at the CTA
+            // barrier, which then orders their TMEM reads after completion.
+            const bool done = warp != 0 || mbar_wait_bounded(bar_mma, phase);
             phase ^= 1u;
             ok = !__syncthreads_or(!done);
             if (!ok) break;
@@ -735,30 +861,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_train_tc(
                 uint8_t* hn = smem + tt.h_off[l + 1];
                 const int kpn = tc.layer[l + 1].Kp;
                 const uint32_t lo = tt.split ? tt.hlo_off - tt.h_off[l + 1] : 0u;
-                for (int c0 = 0; c0 < ly.Np; c0 += 16) {
+                for (int c0 = 16 * half; c0 < ly.Np; c0 += 32) {
                     uint32_t r[16];
                     tmem_ld16(tmem + lane_base + (uint32_t)c0, r);
                     tmem_wait16(r);
                     float v[16];
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] = fmaxf(__uint_as_float(r[i]), 0.0f);
-                    store16(hn, tile_off(t, c0, kpn), tile_off(t, c0 + 8, kpn), v, lo);
+                    store16(hn, tile_off(row, c0, kpn), tile_off(row, c0 + 8, kpn), v, lo);
                 }
                 fence_async_smem();
                 tc_fence_before();
                 __syncthreads();
             } else {
-                uint32_t r[4 * KMAX / 16][16];
+                // This half's lobes: columns [half * 4 KH, (half + 1) * 4 KH).
+                if constexpr (4 * KH >= 16) {
 #pragma unroll
-                for (int c = 0; c < 4 * KMAX / 16; ++c)
-                    if (c * 16 < ly.Np) tmem_ld16(tmem + lane_base + (uint32_t)(c * 16), r[c]);
+                    for (int c = 0; c < 4 * KH / 16; ++c) {
+                        uint32_t r[16];
+                        tmem_ld16(tmem + lane_base + (uint32_t)(half * 4 * KH + 16 * c), r);
+                        tmem_wait16(r);
 #pragma unroll
-                for (int c = 0; c < 4 * KMAX / 16; ++c)
-                    if (c * 16 < ly.Np) tmem_wait16(r[c]);
+                        for (int i = 0; i < 16; ++i) raw[16 * c + i] = __uint_as_float(r[i]);
+                    }
+                } else {
+                    uint32_t r[16];
+                    tmem_ld16(tmem + lane_base, r);
+                    tmem_wait16(r);
 #pragma unroll
-                for (int c = 0; c < 4 * KMAX / 16; ++c)
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) raw[c * 16 + i] = __uint_as_float(r[c][i]);
+                    for (int i = 0; i < 4 * KH; ++i) raw[i] = __uint_as_float(half ? r[4 * KH + i] : r[i]);
+                }
             }
         }
         if (!ok) break;
@@ -770,19 +902,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_train_tc(
             w[2] = dir[2 * ld + j];
             sc = dlogv ? dlogv[j] : -(rad[j] / spdf[j]) * inv_n;
         }
-        float dr[4 * KMAX];
-        const float lv = tc_grad_raw<KMAX>(cfg, raw, w, sc, dr);
-        if (valid) lacc += lv;
-        const int np_last = tc.layer[L - 1].Np;
+        GradHalf<KMAX> gh;
+        const float4 part = gh.pass1(cfg, half, raw, w);
+        xch[half * kTile + row] = part;
+        __syncthreads();
+        const float4 oth = xch[(half ^ 1) * kTile + row];
+        const float lse = lse_combine(part.x, part.y, oth.x, oth.y);
+        const float lsa = lse_combine(part.z, part.w, oth.z, oth.w);
+        if (valid && half == 0) lacc += sc * (lsa - lse);
+        float dr[4 * KH];
+        gh.pass2(lse, lsa, sc, dr);
         const uint32_t dlo = tt.split ? tt.dlo_off - tt.d_off : 0u;
-#pragma unroll
-        for (int c = 0; c < 4 * KMAX / 16; ++c)
-            if (c * 16 < np_last) {
-                float v[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = dr[c * 16 + i];
-                store16(sD, tile_off(t, c * 16, 128), tile_off(t, c * 16 + 8, 128), v, dlo);
-            }
+        store_cols<4 * KH>(sD, row, half * 4 * KH, 128, dr, dlo);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -814,7 +945,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_train_tc(
                 }
                 mma_commit(bar_mma);
             }
-            const bool done = mbar_wait_bounded(bar_mma, phase);
+            const bool done = warp != 0 || mbar_wait_bounded(bar_mma, phase);
             phase ^= 1u;
             ok = !__syncthreads_or(!done);
             if (!ok) break;
@@ -822,12 +953,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_train_tc(
             const uint8_t* hl = smem + tt.h_off[l];
             if (l > 0) {
                 // delta_{l-1} = (D W_l) masked by ReLU'(z_{l-1}) (H_l > 0).
-                for (int c0 = 0; c0 < ly.Kp; c0 += 16) {
+                for (int c0 = 16 * half; c0 < ly.Kp; c0 += 32) {
                     uint32_t r[16];
                     tmem_ld16(tmem + lane_base + (uint32_t)c0, r);
                     tmem_wait16(r);
-                    const uint4 m0 = *reinterpret_cast<const uint4*>(hl + tile_off(t, c0, ly.Kp));
-                    const uint4 m1 = *reinterpret_cast<const uint4*>(hl + tile_off(t, c0 + 8, ly.Kp));
+                    const uint4 m0 = *reinterpret_cast<const uint4*>(hl + tile_off(row, c0, ly.Kp));
+                    const uint4 m1 = *reinterpret_cast<const uint4*>(hl + tile_off(row, c0 + 8, ly.Kp));
                     const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
                     float v[16];
 #pragma unroll
@@ -836,45 +967,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_train_tc(
                         v[2 * i] = hv.x > 0.0f ? __uint_as_float(r[2 * i]) : 0.0f;
                         v[2 * i + 1] = hv.y > 0.0f ? __uint_as_float(r[2 * i + 1]) : 0.0f;
                     }
-                    store16(sD, tile_off(t, c0, 128), tile_off(t, c0 + 8, 128), v, dlo);
+                    store16(sD, tile_off(row, c0, 128), tile_off(row, c0 + 8, 128), v, dlo);
                 }
                 fence_async_smem();
                 tc_fence_before();
                 __syncthreads();
-            } else {
-                // Encoder gradient -> grid scatter (Eq. 11 transposed).
-                float dg[32];
-                for (int c0 = 0; c0 < cfg.grid_feats && c0 < 32; c0 += 16) {
+            } else if (16 * half < cfg.grid_feats) {
+                // Encoder gradient of this half's 16 grid-feature columns ->
+                // grid scatter.
+                float dg[16];
+                {
                     uint32_t r[16];
-                    tmem_ld16(tmem + lane_base + (uint32_t)c0, r);
+                    tmem_ld16(tmem + lane_base + (uint32_t)(16 * half), r);
                     tmem_wait16(r);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) dg[c0 + i] = __uint_as_float(r[i]);
+                    for (int i = 0; i < 16; ++i) dg[i] = __uint_as_float(r[i]);
                 }
                 tc_fence_before();
                 if (valid) {
                     const float x = pos[j], y = pos[ld + j], z = pos[2 * ld + j];
                     const int F = cfg.feat;
-                    for (int lv2 = 0; lv2 < cfg.n_levels; ++lv2) {
-                        const Cell cl = make_cell(x, y, z, cfg.level_res[lv2]);
-                        float* gl = grad + (size_t)cfg.level_off[lv2] * F;
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            const float wc = corner_weight(cl, c);
-                            float* e = gl + (size_t)corner_index(cfg, lv2, cl, c) * F;
-                            if (F == 2) {
-                                atomicAdd(reinterpret_cast<float2*>(e),
-                                          make_float2(wc * dg[lv2 * 2], wc * dg[lv2 * 2 + 1]));
-                            } else if (F == 4) {
-                                atomicAdd(reinterpret_cast<float4*>(e),
-                                          make_float4(wc * dg[lv2 * 4], wc * dg[lv2 * 4 + 1], wc * dg[lv2 * 4 + 2],
-                                                      wc * dg[lv2 * 4 + 3]));
-                            } else {
-                                for (int f = 0; f < F; ++f) atomicAdd(e + f, wc * dg[lv2 * F + f]);
-                            }
-                        }
-                    }
+                    if (F == 2) scatter_levels<2, 8>(cfg, grad, x, y, z, 8 * half, dg);
+                    else if (F == 4) scatter_levels<4, 4>(cfg, grad, x, y, z, 4 * half, dg);
+                    else if (F == 8) scatter_levels<8, 2>(cfg, grad, x, y, z, 2 * half, dg);
+                    else scatter_levels<1, 16>(cfg, grad, x, y, z, 16 * half, dg);
                 }
+            } else {
+                tc_fence_before();
             }
         }
         first = false;
@@ -890,16 +1009,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_train_tc(
     if (ok && !first) {
         for (int l = 0; l < L; ++l) {
             const TcLayer& ly = tc.layer[l];
-            const int o = warp * 32 + (t & 31);
             float* gW = grad + mlp_off + tt.woff[l];
-            for (int c0 = 0; c0 < ly.Kp; c0 += 16) {
+            for (int c0 = 16 * half; c0 < ly.Kp; c0 += 32) {
                 uint32_t r[16];
                 tmem_ld16(tmem + lane_base + tt.dw_col[l] + (uint32_t)c0, r);
                 tmem_wait16(r);
-                if (o < ly.N)
+                if (row < ly.N)
 #pragma unroll
                     for (int i = 0; i < 16; ++i)
-                        if (c0 + i < ly.K) atomicAdd(gW + (int64_t)o * ly.K + c0 + i, __uint_as_float(r[i]));
+                        if (c0 + i < ly.K) atomicAdd(gW + (int64_t)row * ly.K + c0 + i, __uint_as_float(r[i]));
             }
         }
     }
@@ -936,7 +1054,7 @@ npm_status tc_create(npm_handle* h) {
     memset(&t, 0, sizeof(t));
     t.base = h->dc;
     uint32_t off = 0;
-    int maxkp = 0, maxnp = 0;
+    int maxnp = 0;
     for (int l = 0; l < c.n_layers; ++l) {
         TcLayer& ly = t.layer[l];
         ly.K = c.widths[l];
@@ -949,18 +1067,25 @@ npm_status tc_create(npm_handle* h) {
         // both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
         ly.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ly.Np >> 3) << 17) |
                    ((uint32_t)(kTile >> 4) << 24);
-        maxkp = ly.Kp > maxkp ? ly.Kp : maxkp;
         maxnp = ly.Np > maxnp ? ly.Np : maxnp;
     }
     t.w_bytes = (off + 127u) / 128u * 128u;
-    t.a_bytes = (uint32_t)(kTile * maxkp * 2);
+    // Layer 0 gets its own input buffer only when the encoding leaves whole
+    // zero chunks to write once; otherwise it shares the buffer of the
+    // hidden layers (less shared memory, more L1 for the grid gathers).
+    const int enc_width = c.n_levels * c.feat_per_level + (c.mode == NPM_PRODUCT ? 21 : 0);
+    const bool sep0 = (enc_width + 7) / 8 * 8 < t.layer[0].Kp;
+    int maxkp1 = 16;  // widest input of the layers sharing the buffer
+    for (int l = sep0 ? 1 : 0; l < c.n_layers; ++l) maxkp1 = std::max(maxkp1, t.layer[l].Kp);
+    t.a_bytes = (uint32_t)(kTile * maxkp1 * 2);
+    t.a0_bytes = sep0 ? (uint32_t)(kTile * t.layer[0].Kp * 2) : 0u;
     t.split = c.precision == NPM_BF16X3 ? 1 : 0;
     const uint32_t nsplit = t.split ? 2u : 1u;
     uint32_t cols = 32;
     while ((int)cols < maxnp) cols <<= 1;
     t.tmem_cols = cols;
-    t.enc_width = c.n_levels * c.feat_per_level + (c.mode == NPM_PRODUCT ? 21 : 0);
-    s->smem = nsplit * (t.w_bytes + t.a_bytes) + 64;
+    t.enc_width = enc_width;
+    s->smem = nsplit * (t.w_bytes + t.a0_bytes + t.a_bytes) + 64;
     if (s->smem > 200 * 1024 || c.K > 16) {
         delete s;
         return NPM_ERR_UNSUPPORTED;
@@ -1008,7 +1133,8 @@ npm_status tc_create(npm_handle* h) {
         tr.tmem_cols = pw;
         tr.d_off = (off + 127u) / 128u * 128u;
         tr.dlo_off = tr.d_off + kTile * 128 * 2;
-        tr.bar_off = tr.dlo_off + (tr.split ? kTile * 128 * 2 : 0);
+        tr.x_off = tr.dlo_off + (tr.split ? kTile * 128 * 2 : 0);
+        tr.bar_off = tr.x_off + 2 * kTile * 16;
         tr.smem = tr.bar_off + 64;
         s->can_train = fits && pw <= 512 && tr.smem <= 220 * 1024;
     }
@@ -1092,7 +1218,7 @@ static cudaError_t launch_train_tc(npm_handle* h, int64_t n, int64_t ld, const f
     const int64_t ntiles = (n + kTile - 1) / kTile;
     const int g = (int)(ntiles < sms ? ntiles : sms);
     int* status = reinterpret_cast<int*>(h->scalars + 8);
-    kern<<<g < 1 ? 1 : g, kThreads, s->train.smem, st>>>(s->train_cfg, s->train, h->params, s->wblob, n, ld, pos,
+    kern<<<g < 1 ? 1 : g, kTrainThreads, s->train.smem, st>>>(s->train_cfg, s->train, h->params, s->wblob, n, ld, pos,
                                                          aux, dir, rad, spdf, dlogv, 1.0f / (float)n, h->grads,
                                                          h->mlp_off, loss, status);
     return cudaGetLastError();
