@@ -125,6 +125,51 @@ def mlp_flops(w):
     return 2 * sum(a * b for a, b in zip(w.widths[:-1], w.widths[1:]))
 
 
+# Algorithmic work per query of the tensor-core forward on the tiny model
+# (K = 4): transcendentals of the vMF decode, sample and pdf (softmax 4,
+# softplus 8, logistic 16, sine/cosine 16, normalisers 8, reciprocal 1,
+# sampling 6, pdf 4) and about 300 other FP32 operations; 40 bytes of HBM
+# (position, uniforms, direction, pdf).
+TC_MUFU_PER_QUERY = 63
+TC_FP32_OPS_PER_QUERY = 300
+TC_HBM_BYTES_PER_QUERY = 40
+
+
+def tc_roofline(qps, w, pk, up, sms, sm_mhz):
+    """Minimum over the HBM, tensor, MUFU and FP32-lane bounds (queries/s)."""
+    bounds = {
+        "hbm": pk["hbm_gbs"] * 1e9 / TC_HBM_BYTES_PER_QUERY,
+        "tensor": pk["bf16_tflops"] * 1e12 / mlp_flops(w),
+        "mufu": up["mufu_gops"] * 1e9 / TC_MUFU_PER_QUERY,
+        "fp32_lanes": sms * 128 * sm_mhz * 1e6 / TC_FP32_OPS_PER_QUERY,
+    }
+    bound = min(bounds, key=bounds.get)
+    return {"bound": "alu" if bound in ("mufu", "fp32_lanes") else bound, "limiting_unit": bound,
+            "achieved": qps, "peak": bounds[bound], "unit": "queries/s", "frac": qps / bounds[bound],
+            "bounds": bounds,
+            "per_query": {"mufu": TC_MUFU_PER_QUERY, "fp32_ops": TC_FP32_OPS_PER_QUERY,
+                          "hbm_bytes": TC_HBM_BYTES_PER_QUERY, "mlp_flops": mlp_flops(w)},
+            "peak_source": "HBM and BF16 from MEASURED_PEAKS.json; MUFU measured by "
+                           "npm_measure_unit_peaks; FP32 lanes = SMs x 128 x max SM clock"}
+
+
+def train_roofline(sps, w, n_params, pk, up):
+    """Training step bound: dense Adam over every parameter (HBM, 34 B each)
+    plus the grid scatter (levels x 8 two-wide L2 atomics per sample); the
+    forward gathers and the tensor work overlap with them."""
+    adam_s = 34.0 * n_params / (pk["hbm_gbs"] * 1e9)
+    atomics = len(w.level_res) * 8
+    scatter_s_per_sample = atomics / (up["l2_atomic_v2_gops"] * 1e9)
+    n = w.n_train
+    step_s = adam_s + n * scatter_s_per_sample
+    peak = n / step_s
+    return {"bound": "hbm+l2_atomic", "achieved": sps, "peak": peak, "unit": "samples/s",
+            "frac": sps / peak, "adam_bytes_per_step": 34.0 * n_params,
+            "atomics_per_sample": atomics,
+            "peak_source": "HBM from MEASURED_PEAKS.json; two-wide L2 atomics measured by "
+                           "npm_measure_unit_peaks"}
+
+
 def run_reference(args, w, rank):
     """The oracle (FP64 CPU) timed on the host cores, a bounded sample per
     step, on the same workload and metric."""
@@ -350,6 +395,7 @@ def main():
             nt = tw.n_train
             mt = npm.NPM(npm.config_from(tw, max_batch=nt))
             mt.set_params(synth.random_params(tw, 5))
+            n_params = mt.num_params()
             b = synth.train_batch_uniform(tw, nt, seed=5 + rank)
             tb = [torch.from_numpy(a).cuda() for a in (b.pos, b.dir, b.radiance, b.pdf, b.aux)]
             loss = torch.zeros(1, device="cuda")
@@ -367,6 +413,7 @@ def main():
             mt.close()
         nt = synth.PRODUCT_BF16.n_train
         train = {"value": nt * world / (res["split_bf16"] / 1e3), "unit": "train samples/s",
+                 "params": n_params,
                  "ms_per_step": res["split_bf16"],
                  "fp32_kernels": {"value": nt * world / (res["fp32"] / 1e3), "ms_per_step": res["fp32"]},
                  "config": {"workload": synth.PRODUCT_BF16.name, "batch": nt,
@@ -376,6 +423,7 @@ def main():
     if rank != 0:
         return
     pk, pk_src = peaks()
+    unit_peaks = npm.measure_unit_peaks(stream) if not args.no_extras else None
     props = torch.cuda.get_device_properties(local)
     clocks = clk.summary()
     sm_max = clocks.get("sm_max_mhz") or pk.get("sm_max_mhz", 2070.0)
@@ -416,7 +464,15 @@ def main():
         "reduced_precision": reduced,
         "serving": serving,
         "peaks_source": pk_src,
+        "unit_peaks": unit_peaks,
     }
+    if unit_peaks:
+        if reduced:
+            reduced["roofline"] = tc_roofline(reduced["split_bf16"], synth.TINY_BF16, pk, unit_peaks,
+                                              props.multi_processor_count, sm_max)
+        if train:
+            train["roofline"] = train_roofline(train["value"] / world, synth.PRODUCT_BF16,
+                                               train["params"], pk, unit_peaks)
     if not args.no_cpu_baseline and not args.no_extras:
         line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)

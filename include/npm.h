@@ -394,6 +394,34 @@ npm_status npm_check_device_status(npm_handle* h, void* stream);
 /* Thread-local text of the last error returned on this thread. */
 const char* npm_last_error(void);
 
+/* ------------------------------------------------------- unit peaks */
+
+/*
+ * npm_measure_unit_peaks -- measured throughput of the units the hot path's
+ * roofline bounds are built from, on the current device (the paper has no
+ * counterpart; these are the denominators of the L2 and ALU/MUFU bounds,
+ * next to the HBM copy and tensor GEMM peaks measured elsewhere):
+ *   fp32_fma_tflops     packed two-lane FP32 FMA, 2 FLOP per lane-FMA
+ *   fp32_fma_scalar_tflops  the same with scalar FMA
+ *   mufu_gops           MUFU 2^x results per second
+ *   l2_sector_read_gbs  random 32-byte sector reads that bypass L1, from a
+ *                       64 MiB buffer resident in L2, bytes of sectors/s
+ *   l2_atomic_gops      random FP32 atomic adds (no return) into that buffer
+ *   l2_atomic_v2_gops   the same with two-wide FP32 vector atomic adds
+ *   sm_count, max_sm_clock_mhz  the device's SM count and rated clock
+ * Allocates and frees 64 MiB of device memory; runs a few milliseconds of
+ * kernels on `stream` and synchronises it. Not for use inside a capture.
+ * Errors: NPM_ERR_INVALID_ARG (out NULL), NPM_ERR_OOM, NPM_ERR_CUDA.
+ */
+typedef struct npm_unit_peaks {
+    double fp32_fma_tflops, fp32_fma_scalar_tflops, mufu_gops, l2_sector_read_gbs, l2_atomic_gops,
+        l2_atomic_v2_gops;
+    int sm_count;
+    double max_sm_clock_mhz;
+} npm_unit_peaks;
+
+npm_status npm_measure_unit_peaks(npm_unit_peaks* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -342,3 +342,12 @@ class Wavefront:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def measure_unit_peaks(stream=None) -> dict:
+    """Measured FP32 FMA, MUFU, L2 sector-read and L2 atomic throughput of
+    the current device (npm_measure_unit_peaks)."""
+    L = _lib.load()
+    p = _lib.NpmUnitPeaks()
+    _lib.check(L.npm_measure_unit_peaks(C.byref(p), _stream_ptr(stream)), "npm_measure_unit_peaks")
+    return {k: getattr(p, k) for k, _ in p._fields_}

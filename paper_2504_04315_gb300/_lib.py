@@ -57,6 +57,16 @@ class NpmFrameStats(C.Structure):
     ]
 
 
+class NpmUnitPeaks(C.Structure):
+    _fields_ = [
+        ("fp32_fma_tflops", C.c_double), ("fp32_fma_scalar_tflops", C.c_double),
+        ("mufu_gops", C.c_double),
+        ("l2_sector_read_gbs", C.c_double), ("l2_atomic_gops", C.c_double),
+        ("l2_atomic_v2_gops", C.c_double), ("sm_count", C.c_int),
+        ("max_sm_clock_mhz", C.c_double),
+    ]
+
+
 vp = C.c_void_p
 i64 = C.c_int64
 f32 = C.c_float
@@ -98,6 +108,7 @@ SIGNATURES = {
     "npm_server_get_stats": (st, [vp, C.POINTER(NpmServerStats)]),
     "npm_server_destroy": (st, [vp]),
     "npm_eval_pdf_noalloc": (st, [C.POINTER(NpmConfig), vp, i64, vp, vp, vp, i64, vp, vp]),
+    "npm_measure_unit_peaks": (st, [C.POINTER(NpmUnitPeaks), vp]),
 }
 
 _lib = None

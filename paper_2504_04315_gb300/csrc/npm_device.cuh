@@ -51,16 +51,7 @@ __device__ __forceinline__ void lattice_axis(float x, int D, uint32_t& cell, flo
     frac = __fsub_rn(p, (float)c);
 }
 
-__device__ __forceinline__ uint32_t lattice_index(const DevCfg& cfg, int l, uint32_t i, uint32_t j,
-                                                  uint32_t k) {
-    if ((cfg.dense_mask >> l) & 1u) {
-        uint32_t D = (uint32_t)cfg.level_res[l];
-        return i + D * (j + D * k);
-    }
-    return (i ^ (j * 2654435761u) ^ (k * 805459861u)) & cfg.table_mask;
-}
-
-// Corner c (bit0 = +x, bit1 = +y, bit2 = +z): entry index and weight.
+// Cell of a point at one level: lower lattice point and fractions.
 struct Cell {
     uint32_t c[3];
     float f[3];
@@ -74,17 +65,48 @@ __device__ __forceinline__ Cell make_cell(float x, float y, float z, int D) {
     return cl;
 }
 
-__device__ __forceinline__ float corner_weight(const Cell& cl, int corner) {
-    float wx = (corner & 1) ? cl.f[0] : 1.0f - cl.f[0];
-    float wy = (corner & 2) ? cl.f[1] : 1.0f - cl.f[1];
-    float wz = (corner & 4) ? cl.f[2] : 1.0f - cl.f[2];
-    return wx * wy * wz;
+// The 8 corners of a cell at level l (corner c: bit0 = +x, bit1 = +y,
+// bit2 = +z), Eq. 11: entry indices and trilinear weights
+// (wx * wy) * wz with w = f or 1 - f per axis. Lattice point (i, j, k) is
+// entry i + D (j + D k) of a dense level (D^3 <= T) and
+// (i ^ j * 2654435761 ^ k * 805459861) mod T of a hashed one (the
+// Instant-NGP spatial hash; uint32 arithmetic). The per-axis terms are
+// shared: dense corners are b + dx + D dy + D^2 dz with b = i + D (j + D k),
+// hashed ones use (j + 1) * P = j * P + P (mod 2^32). corner_idx8 and
+// corner_w8 compute the two halves separately, so that callers can issue
+// the loads before forming the weights.
+__device__ __forceinline__ void corner_idx8(const DevCfg& cfg, int l, const Cell& cl, uint32_t (&idx)[8]) {
+    if ((cfg.dense_mask >> l) & 1u) {
+        const uint32_t D = (uint32_t)cfg.level_res[l];
+        const uint32_t b = cl.c[0] + D * (cl.c[1] + D * cl.c[2]);
+        const uint32_t dy = D, dz = D * D;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) idx[c] = b + (c & 1) + ((c & 2) ? dy : 0u) + ((c & 4) ? dz : 0u);
+    } else {
+        const uint32_t hx[2] = {cl.c[0], cl.c[0] + 1u};
+        const uint32_t hy0 = cl.c[1] * 2654435761u, hz0 = cl.c[2] * 805459861u;
+        const uint32_t hy[2] = {hy0, hy0 + 2654435761u};
+        const uint32_t hz[2] = {hz0, hz0 + 805459861u};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) idx[c] = (hx[c & 1] ^ hy[(c >> 1) & 1] ^ hz[(c >> 2) & 1]) & cfg.table_mask;
+    }
 }
 
-__device__ __forceinline__ uint32_t corner_index(const DevCfg& cfg, int l, const Cell& cl,
-                                                 int corner) {
-    return lattice_index(cfg, l, cl.c[0] + (corner & 1), cl.c[1] + ((corner >> 1) & 1),
-                         cl.c[2] + ((corner >> 2) & 1));
+__device__ __forceinline__ void corner_w8(const Cell& cl, float (&w)[8]) {
+    const float wx[2] = {1.0f - cl.f[0], cl.f[0]};
+    const float wy[2] = {1.0f - cl.f[1], cl.f[1]};
+    const float wz[2] = {1.0f - cl.f[2], cl.f[2]};
+    float wxy[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) wxy[c] = wx[c & 1] * wy[(c >> 1) & 1];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) w[c] = wxy[c & 3] * wz[(c >> 2) & 1];
+}
+
+__device__ __forceinline__ void corners8(const DevCfg& cfg, int l, const Cell& cl, uint32_t (&idx)[8],
+                                         float (&w)[8]) {
+    corner_idx8(cfg, l, cl, idx);
+    corner_w8(cl, w);
 }
 
 // ------------------------------------------ spherical harmonics (Sec. 4.3)

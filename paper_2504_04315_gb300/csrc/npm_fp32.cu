@@ -31,6 +31,10 @@ constexpr unsigned kFull = 0xffffffffu;
 // in distinct banks.
 __host__ __device__ constexpr int fwd_act_stride(int I) { return 16 * I + 4; }
 
+// Tile groups per CTA of that instance: the register file holds 4 groups at
+// 128 registers a thread, 5 at 96 (enough for the narrow instance only).
+__host__ __device__ constexpr int fwd_max_groups(int I) { return I <= 2 ? 5 : 4; }
+
 // ----------------------------------------------------------- tile GEMM
 
 // Named barrier of tile group `group` (kNT threads; barrier 0 is the CTA's).
@@ -153,40 +157,41 @@ __device__ __forceinline__ void gather_level(const DevCfg& cfg, const float* __r
                                              const Cell& cl, float (&s)[8]) {
     const int F = cfg.feat;
     const float* gl = grid + (size_t)cfg.level_off[l] * F;
+    uint32_t idx[8];
+    corner_idx8(cfg, l, cl, idx);
+    float w[8];
 #pragma unroll
     for (int f = 0; f < 8; ++f) s[f] = 0.0f;
     if (F == 2) {
         float2 v[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-            v[c] = __ldg(reinterpret_cast<const float2*>(gl + (size_t)corner_index(cfg, l, cl, c) * 2));
+        for (int c = 0; c < 8; ++c) v[c] = __ldg(reinterpret_cast<const float2*>(gl) + idx[c]);
+        corner_w8(cl, w);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const float w = corner_weight(cl, c);
-            s[0] = fmaf(w, v[c].x, s[0]);
-            s[1] = fmaf(w, v[c].y, s[1]);
+            s[0] = fmaf(w[c], v[c].x, s[0]);
+            s[1] = fmaf(w[c], v[c].y, s[1]);
         }
     } else if (F == 4) {
         float4 v[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-            v[c] = __ldg(reinterpret_cast<const float4*>(gl + (size_t)corner_index(cfg, l, cl, c) * 4));
+        for (int c = 0; c < 8; ++c) v[c] = __ldg(reinterpret_cast<const float4*>(gl) + idx[c]);
+        corner_w8(cl, w);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const float w = corner_weight(cl, c);
-            s[0] = fmaf(w, v[c].x, s[0]);
-            s[1] = fmaf(w, v[c].y, s[1]);
-            s[2] = fmaf(w, v[c].z, s[2]);
-            s[3] = fmaf(w, v[c].w, s[3]);
+            s[0] = fmaf(w[c], v[c].x, s[0]);
+            s[1] = fmaf(w[c], v[c].y, s[1]);
+            s[2] = fmaf(w[c], v[c].z, s[2]);
+            s[3] = fmaf(w[c], v[c].w, s[3]);
         }
     } else {
+        corner_w8(cl, w);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const float w = corner_weight(cl, c);
-            const float* e = gl + (size_t)corner_index(cfg, l, cl, c) * F;
+            const float* e = gl + (size_t)idx[c] * F;
 #pragma unroll
             for (int f = 0; f < 8; ++f)
-                if (f < F) s[f] = fmaf(w, __ldg(e + f), s[f]);
+                if (f < F) s[f] = fmaf(w[c], __ldg(e + f), s[f]);
         }
     }
 }
@@ -429,7 +434,7 @@ __device__ __forceinline__ void epilogue_tile(int t, const DevCfg& cfg, const fl
 // copy of the weights in shared memory and each walks its own 64-query tiles
 // with its own activation buffers and named barrier.
 template <bool SAMPLE, int NIMAX, int KH>
-__global__ void __launch_bounds__(512, 1) k_forward_fp32(const __grid_constant__ DevCfg cfg,
+__global__ void __launch_bounds__(fwd_max_groups(NIMAX) * kNT, 1) k_forward_fp32(const __grid_constant__ DevCfg cfg,
                                                          const float* __restrict__ grid,
                                                          const float* __restrict__ wfwd,
                                                          const __grid_constant__ QueryBatch qb) {
@@ -610,10 +615,13 @@ __device__ __forceinline__ void grid_scatter(const DevCfg& cfg, const float* den
         const Cell cl = make_cell(x, y, z, cfg.level_res[l]);
         float* gl = ggrid + (size_t)cfg.level_off[l] * F;
         const float* dg = row + l * F;
+        uint32_t idx[8];
+        float ws[8];
+        corners8(cfg, l, cl, idx, ws);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const float w = corner_weight(cl, c);
-            float* e = gl + (size_t)corner_index(cfg, l, cl, c) * F;
+            const float w = ws[c];
+            float* e = gl + (size_t)idx[c] * F;
             if (F == 2) {
                 atomicAdd(reinterpret_cast<float2*>(e), make_float2(w * dg[0], w * dg[1]));
             } else if (F == 4) {
@@ -771,8 +779,11 @@ __global__ void k_grid_indices(DevCfg cfg, int64_t n, int64_t ld, const float* _
         const float x = pos[j], y = pos[ld + j], z = pos[2 * ld + j];
         for (int l = 0; l < cfg.n_levels; ++l) {
             const Cell cl = make_cell(x, y, z, cfg.level_res[l]);
-            for (int c = 0; c < 8; ++c)
-                out[((int64_t)l * 8 + c) * n + j] = (int32_t)corner_index(cfg, l, cl, c);
+            uint32_t idx[8];
+            float w[8];
+            corners8(cfg, l, cl, idx, w);  // the routine every encoder and scatter uses
+#pragma unroll
+            for (int c = 0; c < 8; ++c) out[((int64_t)l * 8 + c) * n + j] = (int32_t)idx[c];
         }
     }
 }
@@ -847,7 +858,7 @@ static cudaError_t launch_fwd_inst(const DevCfg& cfg, const float* grid, const f
     const size_t wbytes = sizeof(float) * (size_t)cfg.fwd_floats;
     const size_t gbytes = sizeof(float) * (size_t)kTQ * fwd_act_stride(I);
     int G = (int)((227 * 1024 - wbytes) / gbytes);
-    if (G > 4) G = 4;
+    if (G > fwd_max_groups(I)) G = fwd_max_groups(I);
     // Tuning override (groups per CTA) for launch-configuration sweeps.
     if (const char* env = getenv("NPM_FP32_GROUPS")) {
         const int g = atoi(env);

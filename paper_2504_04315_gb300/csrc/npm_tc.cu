@@ -103,6 +103,8 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
+// One potentially blocking test of phase `parity` (the thread may sleep in
+// the barrier for a system-dependent time before it returns false).
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -223,6 +225,19 @@ __device__ __forceinline__ float4 widen4(float4 v) { return v; }
 __device__ __forceinline__ float load_feat(const __half* e, int f) { return __half2float(e[f]); }
 __device__ __forceinline__ float load_feat(const float* e, int f) { return __ldg(e + f); }
 
+// Entry index of corner c of a cell (the corner_idx8 formula for one
+// corner). The two-level gather below issues each corner's load as soon as
+// its index is formed, which schedules better there than forming all 16
+// indices first.
+__device__ __forceinline__ uint32_t corner_idx1(const DevCfg& cfg, int l, const Cell& cl, int c) {
+    const uint32_t i = cl.c[0] + (c & 1), j = cl.c[1] + ((c >> 1) & 1), k = cl.c[2] + ((c >> 2) & 1);
+    if ((cfg.dense_mask >> l) & 1u) {
+        const uint32_t D = (uint32_t)cfg.level_res[l];
+        return i + D * (j + D * k);
+    }
+    return (i ^ (j * 2654435761u) ^ (k * 805459861u)) & cfg.table_mask;
+}
+
 // F2: the grid has 2 features per level (compile-time), so two levels' 16
 // corner loads can be in flight before blending; other grids take the
 // generic per-level path (fewer registers).
@@ -255,13 +270,16 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
             float2 v0[8], v1[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                v0[c] = load_feat2(g0, corner_index(cfg, l, c0, c));
-                v1[c] = load_feat2(g1, corner_index(cfg, l + 1, c1, c));
+                v0[c] = load_feat2(g0, corner_idx1(cfg, l, c0, c));
+                v1[c] = load_feat2(g1, corner_idx1(cfg, l + 1, c1, c));
             }
+            float w0s[8], w1s[8];
+            corner_w8(c0, w0s);
+            corner_w8(c1, w1s);
             float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                const float w0 = corner_weight(c0, c), w1 = corner_weight(c1, c);
+                const float w0 = w0s[c], w1 = w1s[c];
                 a0 = fmaf(w0, v0[c].x, a0);
                 a1 = fmaf(w0, v0[c].y, a1);
                 b0 = fmaf(w1, v1[c].x, b0);
@@ -274,14 +292,18 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
     for (; l < lend; ++l) {
         const Cell cl = make_cell(x, y, z, cfg.level_res[l]);
         const GT* gl = grid_h + (size_t)cfg.level_off[l] * F;
-        if (F2 || F == 2) {
+        if (F2) {  // F = 2 (F2 kernels serve exactly the 2-feature grids)
             float s0 = 0.0f, s1 = 0.0f;
+            uint32_t idx[8];
+            corner_idx8(cfg, l, cl, idx);
             float2 v[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) v[c] = load_feat2(gl, corner_index(cfg, l, cl, c));
+            for (int c = 0; c < 8; ++c) v[c] = load_feat2(gl, idx[c]);
+            float ws[8];
+            corner_w8(cl, ws);
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                const float w = corner_weight(cl, c);
+                const float w = ws[c];
                 s0 = fmaf(w, v[c].x, s0);
                 s1 = fmaf(w, v[c].y, s1);
             }
@@ -289,8 +311,9 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
         } else if (F == 4 || F == 8) {
             // One vector load per corner and group of 4 features.
             uint32_t idx[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) idx[c] = corner_index(cfg, l, cl, c);
+            corner_idx8(cfg, l, cl, idx);
+            float ws[8];
+            corner_w8(cl, ws);
             for (int h = 0; h < (F >> 2); ++h) {
                 decltype(load_raw4(gl, 0u, F, 0)) raw[8];
 #pragma unroll
@@ -298,7 +321,7 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
                 float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    const float w = corner_weight(cl, c);
+                    const float w = ws[c];
                     const float4 v = widen4(raw[c]);
                     acc.x = fmaf(w, v.x, acc.x);
                     acc.y = fmaf(w, v.y, acc.y);
@@ -312,9 +335,11 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
         } else {
             // F = 1
             float s = 0.0f;
+            uint32_t idx[8];
+            float ws[8];
+            corners8(cfg, l, cl, idx, ws);
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-                s = fmaf(corner_weight(cl, c), load_feat(gl + corner_index(cfg, l, cl, c), 0), s);
+            for (int c = 0; c < 8; ++c) s = fmaf(ws[c], load_feat(gl + idx[c], 0), s);
             store_one(sA, tile_off(row, l, kp), s, lo);
         }
     }
@@ -436,7 +461,7 @@ __device__ __forceinline__ void tc_decode(const TcCfg& tc, const float (&raw)[4 
 // --------------------------------------------------------------- kernel
 
 template <int KMAX, bool F2>
-__global__ void __launch_bounds__(kThreads) k_forward_tc(const __grid_constant__ TcCfg tc,
+__global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? 6 : 1) k_forward_tc(const __grid_constant__ TcCfg tc,
                                                          const __half* __restrict__ grid_h,
                                                          const uint8_t* __restrict__ wblob,
                                                          const __grid_constant__ QueryBatch qb,
@@ -748,10 +773,13 @@ __device__ __forceinline__ void scatter_levels(const DevCfg& cfg, float* __restr
         if (l < cfg.n_levels) {
             const Cell cl = make_cell(x, y, z, cfg.level_res[l]);
             float* gl = grad + (size_t)cfg.level_off[l] * FF;
+            uint32_t idx[8];
+            float ws[8];
+            corners8(cfg, l, cl, idx, ws);
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                const float wc = corner_weight(cl, c);
-                float* e = gl + (size_t)corner_index(cfg, l, cl, c) * FF;
+                const float wc = ws[c];
+                float* e = gl + (size_t)idx[c] * FF;
                 if constexpr (FF == 1) {
                     atomicAdd(e, wc * dg[q]);
                 } else if constexpr (FF == 2) {
