@@ -372,6 +372,31 @@ npm_status npm_get_grads(npm_handle* h, float* host, int64_t count);
 float* npm_params_device(npm_handle* h);
 float* npm_grads_device(npm_handle* h);
 
+/*
+ * Moving average of the weights for inference (Sec. 5.3: inference applies
+ * an exponential moving average of the weights of the previous training
+ * steps, which damps the noise of the Monte Carlo gradients).
+ *   decay in (0, 1): from now on every Adam step also updates
+ *            e <- decay * e + (1 - decay) * p over all parameters (grid and
+ *            MLP, fused into the Adam kernel), and every inference call
+ *            (npm_query_sample, npm_query_sample_host, npm_eval_pdf, the
+ *            server) evaluates the network with e; training keeps using p.
+ *            The first enable starts e at the current parameters; calling
+ *            again with another decay keeps e. npm_set_params restarts e at
+ *            the new parameters.
+ *   decay 0: off; inference evaluates p again (e is released).
+ * Allocates the average and its padded weight copies on the first enable
+ * (not a hot call) and synchronises `stream`. A wavefront driver captures
+ * its frame graph on its first run: enable or disable the average before
+ * that. Checkpoints (npm_save) do not hold e.
+ * Errors: NPM_ERR_INVALID_ARG (decay outside [0, 1)), NPM_ERR_OOM.
+ */
+npm_status npm_set_ema(npm_handle* h, float decay, void* stream);
+
+/* The moving average in the public parameter layout (host buffer of
+ * npm_num_params floats); NPM_ERR_INVALID_ARG when it is off. */
+npm_status npm_get_ema_params(npm_handle* h, float* host, int64_t count);
+
 /* Adam state: step counter and moments (host buffers of npm_num_params). */
 npm_status npm_get_adam(npm_handle* h, int* step, float* m_host, float* v_host);
 npm_status npm_set_adam(npm_handle* h, int step, const float* m_host, const float* v_host);

@@ -78,6 +78,7 @@ def lib():
             "orc_train_grad": (d, [P(OrcCfg), vp, i64, vp, vp, vp, vp, vp, i64, vp]),
             "orc_train_loss": (d, [P(OrcCfg), vp, i64, vp, vp, vp, vp, vp, i64]),
             "orc_adam": (None, [i64, vp, vp, vp, vp, C.c_int, d, d, d, d]),
+            "orc_ema": (None, [i64, vp, vp, d]),
             "orc_num_threads": (C.c_int, []),
         }
         for name, (res, args) in sig.items():
@@ -278,6 +279,13 @@ def adam(p, g, m, v, t: int, lr: float, b1: float, b2: float, eps: float):
     for a in (p, g, m, v):
         assert a.dtype == np.float64 and a.flags.c_contiguous
     lib().orc_adam(p.size, _p(p), _p(g), _p(m), _p(v), int(t), lr, b1, b2, eps)
+
+
+def ema(e, p, decay: float):
+    """In place on float64 array e: e <- decay e + (1 - decay) p (Sec. 5.3)."""
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    assert e.dtype == np.float64 and e.flags.c_contiguous and e.size == p.size
+    lib().orc_ema(e.size, _p(e), _p(p), float(decay))
 
 
 def num_threads() -> int:

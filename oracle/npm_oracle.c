@@ -595,6 +595,12 @@ void orc_adam(int64_t n, double* p, const double* g, double* m, double* v, int t
     }
 }
 
+/* Sec. 5.3, inference weights: the exponential moving average of the
+ * parameters after each training step, e <- d e + (1 - d) p. */
+void orc_ema(int64_t n, double* e, const double* p, double d) {
+    for (int64_t i = 0; i < n; ++i) e[i] = d * e[i] + (1.0 - d) * p[i];
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

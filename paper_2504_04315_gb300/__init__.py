@@ -197,6 +197,17 @@ class NPM:
                    "npm_get_grads")
         return a
 
+    def set_ema(self, decay: float, stream=None):
+        """Inference evaluates the moving average of the weights (npm_set_ema);
+        decay 0 turns it off."""
+        _lib.check(self._L.npm_set_ema(self._h, float(decay), _stream_ptr(stream)), "npm_set_ema")
+
+    def get_ema_params(self) -> np.ndarray:
+        a = np.empty(self.num_params(), dtype=np.float32)
+        _lib.check(self._L.npm_get_ema_params(self._h, a.ctypes.data_as(C.c_void_p), a.size),
+                   "npm_get_ema_params")
+        return a
+
     def get_adam(self):
         n = self.num_params()
         m = np.empty(n, dtype=np.float32)

@@ -88,6 +88,8 @@ SIGNATURES = {
     "npm_get_grads": (st, [vp, vp, i64]),
     "npm_params_device": (vp, [vp]),
     "npm_grads_device": (vp, [vp]),
+    "npm_set_ema": (st, [vp, f32, vp]),
+    "npm_get_ema_params": (st, [vp, vp, i64]),
     "npm_get_adam": (st, [vp, C.POINTER(C.c_int), vp, vp]),
     "npm_set_adam": (st, [vp, C.c_int, vp, vp]),
     "npm_grid_indices": (st, [vp, i64, vp, i64, vp, vp]),

@@ -110,10 +110,23 @@ npm_status check_call(npm_handle* h, int64_t n, int64_t ld, const void* pos, con
 // Device-side count of completed Adam steps (scalars[16]).
 int* step_dev(npm_handle* h) { return reinterpret_cast<int*>(h->scalars + 16); }
 
+// Padded FP32 forward weights of the moving average (inference).
+npm_status arrange_inference_weights(npm_handle* h, cudaStream_t st) {
+    if (h->ema)
+        NPM_CUDA(npm::launch_arrange_weights(h->dc, h->ema + h->mlp_off, h->wfwd_inf, nullptr, st),
+                 "arrange ema weights");
+    return NPM_OK;
+}
+
+// Every copy derived from the parameters: the FP32 kernels' padded weights,
+// the FP16 grid and the tensor-core weights (of the moving average too,
+// when inference evaluates it).
 npm_status refresh_derived(npm_handle* h, cudaStream_t st) {
     NPM_CUDA(npm::launch_arrange_weights(h->dc, h->params + h->mlp_off, h->wfwd, h->wbwd, st),
              "arrange weights");
-    if (h->grid_h) NPM_CUDA(npm::launch_to_half(h->ng, h->params, h->grid_h, st), "grid fp16 copy");
+    npm_status s = arrange_inference_weights(h, st);
+    if (s != NPM_OK) return s;
+    if (h->grid_h) NPM_CUDA(npm::launch_to_half(h->ng, inf_params(h), h->grid_h, st), "grid fp16 copy");
     if (h->tc) NPM_CUDA(npm::tc_refresh_weights(h, st), "bf16 weight copy");
     return NPM_OK;
 }
@@ -272,8 +285,8 @@ npm_status npm_destroy(npm_handle* h) {
     if (!h) return NPM_OK;
     cudaDeviceSynchronize();
     if (h->tc) npm::tc_destroy(h);
-    void* ptrs[] = {h->params, h->grads, h->adam_m, h->adam_v, h->wfwd,
-                    h->wbwd,   h->scalars, h->stage, h->grid_h};
+    void* ptrs[] = {h->params, h->grads, h->adam_m, h->adam_v,   h->wfwd,  h->wbwd,
+                    h->scalars, h->stage, h->grid_h, h->ema, h->wfwd_inf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < 2; ++i)
@@ -307,6 +320,9 @@ static npm_status copy_public(npm_handle* h, float* dev, float* host, int64_t co
 npm_status npm_set_params(npm_handle* h, const float* host, int64_t count) {
     npm_status s = copy_public(h, h ? h->params : nullptr, const_cast<float*>(host), count, true);
     if (s != NPM_OK) return s;
+    if (h->ema)  // the average restarts from the new parameters
+        NPM_CUDA(cudaMemcpy(h->ema, h->params, h->n_int * sizeof(float), cudaMemcpyDeviceToDevice),
+                 "reset ema");
     if ((s = refresh_derived(h, 0)) != NPM_OK) return s;
     NPM_CUDA(cudaDeviceSynchronize(), "npm_set_params");
     return NPM_OK;
@@ -314,6 +330,46 @@ npm_status npm_set_params(npm_handle* h, const float* host, int64_t count) {
 
 npm_status npm_get_params(npm_handle* h, float* host, int64_t count) {
     return copy_public(h, h ? h->params : nullptr, host, count, false);
+}
+
+npm_status npm_set_ema(npm_handle* h, float decay, void* stream) {
+    if (!h) return fail(NPM_ERR_INVALID_ARG, "handle is NULL");
+    if (!(decay >= 0.0f && decay < 1.0f)) return fail(NPM_ERR_INVALID_ARG, "decay must be in [0, 1)");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (decay == 0.0f) {
+        if (h->ema) {
+            NPM_CUDA(cudaStreamSynchronize(st), "synchronise");
+            cudaFree(h->ema);
+            cudaFree(h->wfwd_inf);
+            h->ema = h->wfwd_inf = nullptr;
+        }
+        h->ema_decay = 0.0f;
+        npm_status s = refresh_derived(h, st);
+        if (s != NPM_OK) return s;
+        NPM_CUDA(cudaStreamSynchronize(st), "npm_set_ema");
+        return NPM_OK;
+    }
+    if (!h->ema) {
+        npm_status s;
+        if ((s = dalloc(&h->ema, h->n_int, "ema")) != NPM_OK) return s;
+        if ((s = dalloc(&h->wfwd_inf, (size_t)h->dc.fwd_floats, "ema forward weights")) != NPM_OK) {
+            cudaFree(h->ema);
+            h->ema = nullptr;
+            return s;
+        }
+        NPM_CUDA(cudaMemcpyAsync(h->ema, h->params, h->n_int * sizeof(float), cudaMemcpyDeviceToDevice, st),
+                 "start ema");
+    }
+    h->ema_decay = decay;
+    npm_status s = refresh_derived(h, st);
+    if (s != NPM_OK) return s;
+    NPM_CUDA(cudaStreamSynchronize(st), "npm_set_ema");
+    return NPM_OK;
+}
+
+npm_status npm_get_ema_params(npm_handle* h, float* host, int64_t count) {
+    if (h && !h->ema) return fail(NPM_ERR_INVALID_ARG, "the moving average is off (npm_set_ema)");
+    return copy_public(h, h ? h->ema : nullptr, host, count, false);
 }
 
 npm_status npm_get_grads(npm_handle* h, float* host, int64_t count) {
@@ -357,7 +413,7 @@ npm_status npm_query_sample(npm_handle* h, int64_t n, const float* pos, const fl
     if (n == 0) return NPM_OK;
     cudaStream_t st = (cudaStream_t)stream;
     if (h->tc) return npm::tc_query(h, n, ld, pos, aux, u, uniform_frac, true, dir_out, pdf_out, mix_out, st);
-    NPM_CUDA(npm::launch_forward_fp32(h->dc, h->params, h->wfwd, n, ld, pos, aux, u, uniform_frac,
+    NPM_CUDA(npm::launch_forward_fp32(h->dc, inf_params(h), inf_wfwd(h), n, ld, pos, aux, u, uniform_frac,
                                       true, dir_out, pdf_out, mix_out, st),
              "query_sample launch");
     return NPM_OK;
@@ -426,7 +482,7 @@ npm_status npm_eval_pdf(npm_handle* h, int64_t n, const float* pos, const float*
     if (n == 0) return NPM_OK;
     cudaStream_t st = (cudaStream_t)stream;
     if (h->tc) return npm::tc_query(h, n, ld, pos, aux, dir, 0.0f, false, nullptr, pdf_out, nullptr, st);
-    NPM_CUDA(npm::launch_forward_fp32(h->dc, h->params, h->wfwd, n, ld, pos, aux, dir, 0.0f, false,
+    NPM_CUDA(npm::launch_forward_fp32(h->dc, inf_params(h), inf_wfwd(h), n, ld, pos, aux, dir, 0.0f, false,
                                       nullptr, pdf_out, nullptr, st),
              "eval_pdf launch");
     return NPM_OK;
@@ -455,12 +511,14 @@ static npm_status adam_impl(npm_handle* h, const float* loss, cudaStream_t st) {
     int* status = reinterpret_cast<int*>(h->scalars + 8);
     NPM_CUDA(npm::launch_adam(h->n_int, h->params, h->grads, h->adam_m, h->adam_v, h->cfg.lr,
                               h->cfg.beta1, h->cfg.beta2, h->cfg.eps, step_dev(h), loss, status,
-                              h->grid_h, h->grid_h ? (h->ng / 4) * 4 : 0, st),
+                              h->grid_h, h->grid_h ? (h->ng / 4) * 4 : 0, h->ema, h->ema_decay, st),
              "adam launch");
     if (h->grid_h && h->ng % 4)
-        NPM_CUDA(npm::launch_to_half(h->ng, h->params, h->grid_h, st), "grid fp16 tail");
+        NPM_CUDA(npm::launch_to_half(h->ng, inf_params(h), h->grid_h, st), "grid fp16 tail");
     NPM_CUDA(npm::launch_arrange_weights(h->dc, h->params + h->mlp_off, h->wfwd, h->wbwd, st),
              "arrange weights");
+    npm_status s = arrange_inference_weights(h, st);
+    if (s != NPM_OK) return s;
     if (h->tc) NPM_CUDA(npm::tc_refresh_weights(h, st), "bf16 weight copy");
     return NPM_OK;
 }

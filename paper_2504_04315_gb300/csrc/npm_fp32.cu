@@ -702,10 +702,11 @@ __global__ void k_arrange_weights(DevCfg cfg, const float* __restrict__ mlp,
             const int k = i / npf, nn = i % npf;
             wfwd[cfg.off_fwd[l] + i] = nn < N ? mlp[woff + (int64_t)nn * K + k] : 0.0f;
         }
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N * npb; i += gridDim.x * blockDim.x) {
-            const int nn = i / npb, k = i % npb;
-            wbwd[cfg.off_bwd[l] + i] = k < K ? mlp[woff + (int64_t)nn * K + k] : 0.0f;
-        }
+        if (wbwd)  // backward copy (training only)
+            for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N * npb; i += gridDim.x * blockDim.x) {
+                const int nn = i / npb, k = i % npb;
+                wbwd[cfg.off_bwd[l] + i] = k < K ? mlp[woff + (int64_t)nn * K + k] : 0.0f;
+            }
         woff += (int64_t)K * N;
     }
 }
@@ -715,11 +716,14 @@ __global__ void k_arrange_weights(DevCfg cfg, const float* __restrict__ mlp,
 // captured graphs replay correctly (k_step_done advances it afterwards).
 // Skips the update when *loss is not finite and flags it. Clears the
 // gradient. Optionally refreshes an FP16 copy of the first n_half parameters
-// (the grid).
+// (the grid). With ema set, also the exponential moving average
+// e <- d e + (1 - d) p of the updated parameters that inference evaluates
+// (Sec. 5.3); the FP16 copy (inference only) is then taken from e.
 __global__ void k_adam(int64_t n4, float4* __restrict__ p, float4* __restrict__ g,
                        float4* __restrict__ m, float4* __restrict__ v, float lr, float b1, float b2,
                        float eps, const int* __restrict__ steps, const float* __restrict__ loss,
-                       int* __restrict__ status, __half2* __restrict__ half_copy, int64_t n_half4) {
+                       int* __restrict__ status, __half2* __restrict__ half_copy, int64_t n_half4,
+                       float4* __restrict__ ema, float ema_decay) {
     const bool skip = loss != nullptr && !isfinite(*loss);
     if (skip && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatusNumeric);
     const float t = (float)(*steps + 1);
@@ -760,9 +764,20 @@ __global__ void k_adam(int64_t n4, float4* __restrict__ p, float4* __restrict__ 
             m[i] = mm[u];
             v[i] = vv[u];
             p[i] = pp[u];
+            float4 inf = pp[u];
+            if (ema) {
+                float4 e = ema[i];
+                const float d = ema_decay, d1 = 1.0f - ema_decay;
+                e.x = d * e.x + d1 * pp[u].x;
+                e.y = d * e.y + d1 * pp[u].y;
+                e.z = d * e.z + d1 * pp[u].z;
+                e.w = d * e.w + d1 * pp[u].w;
+                ema[i] = e;
+                inf = e;
+            }
             if (half_copy && i < n_half4) {
-                half_copy[2 * i] = __floats2half2_rn(pp[u].x, pp[u].y);
-                half_copy[2 * i + 1] = __floats2half2_rn(pp[u].z, pp[u].w);
+                half_copy[2 * i] = __floats2half2_rn(inf.x, inf.y);
+                half_copy[2 * i + 1] = __floats2half2_rn(inf.z, inf.w);
             }
         }
     }
@@ -942,7 +957,8 @@ cudaError_t launch_arrange_weights(const DevCfg& cfg, const float* mlp, float* w
 
 cudaError_t launch_adam(int64_t n, float* p, float* g, float* m, float* v, float lr, float b1,
                         float b2, float eps, int* steps, const float* loss, int* status,
-                        __half* half_copy, int64_t n_half, cudaStream_t st) {
+                        __half* half_copy, int64_t n_half, float* ema, float ema_decay,
+                        cudaStream_t st) {
     const int64_t n4 = n / 4;
     int grid = (int)((n4 + 255) / 256);
     const int cap = sm_count() * 16;
@@ -951,7 +967,8 @@ cudaError_t launch_adam(int64_t n, float* p, float* g, float* m, float* v, float
     k_adam<<<grid, 256, 0, st>>>(n4, reinterpret_cast<float4*>(p), reinterpret_cast<float4*>(g),
                                  reinterpret_cast<float4*>(m), reinterpret_cast<float4*>(v), lr, b1,
                                  b2, eps, steps, loss, status,
-                                 reinterpret_cast<__half2*>(half_copy), n_half / 4);
+                                 reinterpret_cast<__half2*>(half_copy), n_half / 4,
+                                 reinterpret_cast<float4*>(ema), ema_decay);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_step_done<<<1, 32, 0, st>>>(steps);

@@ -34,7 +34,18 @@ struct npm_handle {
     size_t fwd_smem = 0, train_smem = 0;
     int step = 0;
     npm::TcState* tc = nullptr;  // tensor-core (BF16) path state
+    // Exponential moving average of the parameters (Sec. 5.3), evaluated by
+    // inference when enabled: ema (n_int, internal layout) and its padded
+    // forward weights; the FP16 grid copy and the tensor-core inference
+    // weights are then derived from ema too.
+    float* ema = nullptr;
+    float* wfwd_inf = nullptr;
+    float ema_decay = 0.0f;
 };
+
+// Parameters and FP32 forward weights that inference evaluates.
+inline const float* inf_params(const npm_handle* h) { return h->ema ? h->ema : h->params; }
+inline const float* inf_wfwd(const npm_handle* h) { return h->ema ? h->wfwd_inf : h->wfwd; }
 
 namespace npm {
 // Validates cfg and derives the kernels' view of it; ng / nmlp receive the

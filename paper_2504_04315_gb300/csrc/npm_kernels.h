@@ -34,10 +34,12 @@ cudaError_t launch_arrange_weights(const DevCfg& cfg, const float* mlp, float* w
                                    cudaStream_t st);
 
 // Adam at step *steps + 1 (device counter, advanced on the stream after the
-// update).
+// update). ema (or NULL): moving average updated with ema_decay; the FP16
+// copy is then taken from it.
 cudaError_t launch_adam(int64_t n, float* p, float* g, float* m, float* v, float lr, float b1,
                         float b2, float eps, int* steps, const float* loss, int* status,
-                        __half* half_copy, int64_t n_half, cudaStream_t st);
+                        __half* half_copy, int64_t n_half, float* ema, float ema_decay,
+                        cudaStream_t st);
 
 cudaError_t launch_grid_indices(const DevCfg& cfg, int64_t n, int64_t ld, const float* pos,
                                 int32_t* out, cudaStream_t st);

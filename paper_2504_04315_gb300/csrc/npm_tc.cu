@@ -1062,7 +1062,8 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(
 
 struct TcState {
     TcCfg cfg;
-    uint8_t* wblob = nullptr;
+    uint8_t* wblob = nullptr;      // BF16 weights of the training parameters
+    uint8_t* wblob_inf = nullptr;  // of the moving average, when inference uses it
     size_t smem = 0;
     int grid = 0;
     TcCfg train_cfg;     // single-pass BF16 copy of cfg for training
@@ -1179,12 +1180,23 @@ npm_status tc_create(npm_handle* h) {
 void tc_destroy(npm_handle* h) {
     if (!h->tc) return;
     if (h->tc->wblob) cudaFree(h->tc->wblob);
+    if (h->tc->wblob_inf) cudaFree(h->tc->wblob_inf);
     delete h->tc;
     h->tc = nullptr;
 }
 
 cudaError_t tc_refresh_weights(npm_handle* h, cudaStream_t st) {
-    k_tc_weights<<<16, 256, 0, st>>>(h->tc->cfg, h->params + h->mlp_off, h->tc->wblob);
+    TcState* s = h->tc;
+    k_tc_weights<<<16, 256, 0, st>>>(s->cfg, h->params + h->mlp_off, s->wblob);
+    if (h->ema) {
+        if (!s->wblob_inf) {
+            const size_t bytes = (s->cfg.split ? 2u : 1u) * (size_t)s->cfg.w_bytes;
+            cudaError_t e = cudaMalloc(&s->wblob_inf, bytes);
+            if (e != cudaSuccess) return e;
+            cudaMemsetAsync(s->wblob_inf, 0, bytes, st);
+        }
+        k_tc_weights<<<16, 256, 0, st>>>(s->cfg, h->ema + h->mlp_off, s->wblob_inf);
+    }
     return cudaGetLastError();
 }
 
@@ -1225,7 +1237,8 @@ static cudaError_t launch_tc(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaS
     int64_t g = (int64_t)per_sm * sms;
     if (g > hint) g = hint < 1 ? 1 : hint;
     int* status = reinterpret_cast<int*>(h->scalars + 8);
-    kern<<<(int)g, kThreads, s->smem, st>>>(s->cfg, h->grid_h, s->wblob, qb, status);
+    const uint8_t* wb = h->ema ? s->wblob_inf : s->wblob;  // inference weights
+    kern<<<(int)g, kThreads, s->smem, st>>>(s->cfg, h->grid_h, wb, qb, status);
     return cudaGetLastError();
 }
 

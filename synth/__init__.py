@@ -129,6 +129,15 @@ PRODUCT_BF16 = Workload(
     widths=[64, 64, 64, 64, 32], K=8, precision=BF16X3,
     n_query=1 << 19, n_train=1 << 19, lr=1e-2, beta1=0.9, beta2=0.99)
 
+# The paper's own shape (Sec. 5.3): L = 8 dense levels whose resolution grows
+# geometrically from D = 8 to D = 86 (D_l = floor(8 (86/8)^(l/7))), F = 4
+# features (3.95 M grid parameters), three hidden layers of width 64, K = 8.
+RES8_PAPER = [8, 11, 15, 22, 31, 43, 61, 86]
+PAPER_OWN = Workload(
+    name="paper's own shape: 8 dense levels D 8..86 x 4 feats, MLP 32-64-64-64-32, K=8, fp32",
+    mode=RADIANCE, level_res=list(RES8_PAPER), feat=4, log2_table=20,
+    widths=[32, 64, 64, 64, 32], K=8, n_query=1 << 20, n_train=1 << 18)
+
 # Finite-difference net: 2 dense levels, hidden width 8, K=2.
 FD_TINY = Workload(
     name="finite-difference net: 2 dense levels (4, 8), hidden 8, K=2",
@@ -144,6 +153,10 @@ WORKLOADS = {
     "paper_hash": PAPER_HASH,
     "tiny_bf16": TINY_BF16,
     "product_bf16": PRODUCT_BF16,
+    "paper_own": PAPER_OWN,
+    "paper_own_bf16": PAPER_OWN.with_(
+        name="paper's own shape: 8 dense levels D 8..86 x 4 feats, MLP 32-64-64-64-32, K=8, split-bf16",
+        precision=BF16X3),
 }
 
 

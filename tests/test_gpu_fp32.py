@@ -33,7 +33,7 @@ def edge_positions():
     return np.array(pts, dtype=np.float32).T
 
 
-@pytest.mark.parametrize("w", [synth.TINY, synth.PAPER_HASH, PRODUCT_SMALL])
+@pytest.mark.parametrize("w", [synth.TINY, synth.PAPER_HASH, PRODUCT_SMALL, synth.PAPER_OWN])
 def test_grid_indices_bit_exact(w):
     n = 50_000
     pos = np.concatenate([synth.positions(5, n), edge_positions()], axis=1)
@@ -46,7 +46,8 @@ def test_grid_indices_bit_exact(w):
 
 
 @pytest.mark.parametrize("w,n", [(synth.TINY, 4096 + 37), (PRODUCT_SMALL, 3000),
-                                 (synth.TINY.with_(kappa_act=synth.EXP), 2048)])
+                                 (synth.TINY.with_(kappa_act=synth.EXP), 2048),
+                                 (synth.PAPER_OWN, 3000)])
 def test_query_sample_parity(w, n):
     params = synth.random_params(w, 3, kappa_boost=6.0 if w.kappa_act == synth.SOFTPLUS else 1.0)
     pos = synth.positions(7, n)
@@ -162,7 +163,7 @@ def _grad_blocks(w, g):
 
 @pytest.mark.parametrize("w,n", [(synth.TINY, 4096), (PRODUCT_SMALL, 4096),
                                  (synth.TINY.with_(kappa_act=synth.EXP), 2048),
-                                 (synth.PAPER_HASH, 4096)])
+                                 (synth.PAPER_HASH, 4096), (synth.PAPER_OWN, 4096)])
 def test_gradient_parity(w, n):
     # Table 1's exp mapping of kappa needs milder raw outputs than softplus.
     params = synth.random_params(w, 12, kappa_boost=6.0 if w.kappa_act == synth.SOFTPLUS else 1.0)

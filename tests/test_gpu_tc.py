@@ -69,6 +69,7 @@ def test_tc_pdf_parity(w, n):
 
 @pytest.mark.parametrize("w,n", [(synth.TINY_BF16, 1 << 16),
                                  (synth.PAPER_HASH.with_(precision=synth.BF16X3), 1 << 14),
+                                 (synth.PAPER_OWN.with_(precision=synth.BF16X3), 1 << 14),
                                  (PRODUCT_SMALL.with_(precision=synth.BF16X3), 4096),
                                  (synth.PRODUCT_BF16.with_(precision=synth.BF16X3), 1 << 14)])
 def test_tc_split_bf16_parity(w, n):
@@ -123,6 +124,7 @@ def test_tc_matches_fp32_path_on_lobe_choice():
 
 @pytest.mark.parametrize("w,n", [(synth.TINY_BF16, 4096), (PRODUCT_SMALL.with_(precision=synth.BF16X3), 4096),
                                  (synth.PAPER_HASH.with_(precision=synth.BF16X3), 4096),
+                                 (synth.PAPER_OWN.with_(precision=synth.BF16X3), 4096),
                                  (synth.PRODUCT_BF16, 3000),
                                  (synth.TINY_BF16.with_(precision=synth.BF16), 4096)])
 def test_tc_gradient_parity(w, n):

@@ -496,6 +496,27 @@ def test_single_lobe_fit_is_weighted_vmf_mle():
 
 # -------------------------------------------------------------- a11: Adam
 
+def test_ema_closed_form():
+    """Sec. 5.3 weight averaging: with the parameters held at p, t updates of
+    e <- d e + (1 - d) p leave e_t = p + d^t (e_0 - p); d = 0 copies p; the
+    average of a parameter path stays inside its range."""
+    rng = np.random.default_rng(21)
+    n, d = 257, 0.9
+    e0, p = rng.standard_normal(n), rng.standard_normal(n)
+    e = e0.copy()
+    for _ in range(7):
+        oracle.ema(e, p, d)
+    assert np.allclose(e, p + d ** 7 * (e0 - p), rtol=0, atol=1e-14)
+    e = e0.copy()
+    oracle.ema(e, p, 0.0)
+    assert np.array_equal(e, p)
+    path = rng.uniform(-1.0, 2.0, size=(20, n))
+    e = path[0].copy()
+    for q in path[1:]:
+        oracle.ema(e, q, 0.7)
+    assert np.all(e >= path.min(axis=0) - 1e-15) and np.all(e <= path.max(axis=0) + 1e-15)
+
+
 def test_adam_closed_form_two_steps():
     rng = np.random.default_rng(14)
     n = 1000
