@@ -125,6 +125,10 @@ def mlp_flops(w):
     return 2 * sum(a * b for a, b in zip(w.widths[:-1], w.widths[1:]))
 
 
+# DRAM bytes of one k_forward_fp32 launch on the paper-shaped workload
+# (2^20 queries) from the ncu capture summarised in profiles/.
+FP32_FORWARD_DRAM_BYTES = 66717952 + 9522688
+
 # Algorithmic work per query of the tensor-core forward on the tiny model
 # (K = 4): transcendentals of the vMF decode, sample and pdf (softmax 4,
 # softplus 8, logistic 16, sine/cosine 16, normalisers 8, reciprocal 1,
@@ -455,7 +459,12 @@ def main():
         # arrangement, the loss copy, and on tensor cores the BF16 weights.
         "gpu_launches": K * ((6 if w.precision != synth.FP32 else 5) if train_mode else 1),
         "roofline": ({"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                      "frac": achieved / alu_peak, "traffic": None,
+                      "frac": achieved / alu_peak, "traffic": FP32_FORWARD_DRAM_BYTES,
+                      "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one 2^20-query "
+                                      "launch (profiles/k_forward_fp32_paper_hash_2e20.md); ncu flushes "
+                                      "the caches before the capture, so it includes the 41.7 MB FP32 "
+                                      "grid table that stays in L2 between calls; algorithmic HBM "
+                                      "bytes are 40 per query (41.9 MB)",
                       "kernel": "k_forward_fp32<sample>",
                       "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"}
                      if (w.precision == synth.FP32 and not train_mode) else None),

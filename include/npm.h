@@ -169,6 +169,10 @@ npm_status npm_eval_pdf(npm_handle* h, int64_t n, const float* pos, const float*
  * skips the update on the device (parameters and moments unchanged, the step
  * counter still advances) and records NPM_ERR_NUMERIC in the device status
  * word, which npm_check_device_status reports.
+ * Training keeps a tile's activations of every layer on chip; networks whose
+ * tiles do not fit (for example 128-wide hidden layers with a 128-wide
+ * input) return NPM_ERR_UNSUPPORTED here and in npm_backward before anything
+ * is launched; inference supports every valid configuration.
  */
 npm_status npm_train_step(npm_handle* h, int64_t n, const float* pos, const float* aux,
                           const float* dir, const float* radiance, const float* sample_pdf,

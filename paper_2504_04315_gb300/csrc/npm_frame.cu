@@ -92,13 +92,20 @@ __device__ __forceinline__ void stamp(const WfState& s, int slot) {
     if ((int64_t)f < s.max_frames) s.stamps[f * (s.bounces + 2) + slot] = globaltimer();
 }
 
+// Sampling uniforms of path p at bounce b, written at queue slot i.
+__device__ __forceinline__ void write_uniforms(const WfState& s, uint64_t ku, int64_t i, uint64_t p) {
+    for (int r = 0; r < 4; ++r) s.u[r * s.P + i] = uni(ku, r * (uint64_t)s.P + p);
+}
+
+// Camera rays of the frame: positions, path ids and bounce 0's uniforms.
 __global__ void k_wf_start(WfState s) {
     const uint64_t f = *s.frame;
-    const uint64_t kp = key(s.seed, f, 0, 1);
+    const uint64_t kp = key(s.seed, f, 0, 1), ku = key(s.seed, f, 0, 2);
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < s.P;
          p += (int64_t)gridDim.x * blockDim.x) {
         for (int r = 0; r < 3; ++r) s.pos[0][r * s.P + p] = uni(kp, (uint64_t)(r * s.P + p));
         s.pid[0][p] = (int32_t)p;
+        write_uniforms(s, ku, p, (uint64_t)p);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         s.count[0] = s.P;
@@ -112,23 +119,16 @@ __global__ void k_wf_stamp(WfState s, int slot) {
     if (threadIdx.x == 0 && blockIdx.x == 0) stamp(s, slot);
 }
 
-__global__ void k_wf_uniforms(WfState s, int b, int src) {
-    const uint64_t f = *s.frame;
-    const int64_t n = s.count[src];
-    const uint64_t ku = key(s.seed, f, b, 2);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t p = (uint64_t)s.pid[src][i];
-        for (int r = 0; r < 4; ++r) s.u[r * s.P + i] = uni(ku, r * (uint64_t)s.P + p);
-    }
-}
-
-// Radiance estimate, training record, survival and compaction of one bounce.
+// Radiance estimate, training record, survival and compaction of one
+// bounce; each survivor also gets the next bounce's uniforms at its new
+// queue slot (this bounce's query kernel has consumed the old ones).
 __global__ void k_wf_advance(WfState s, int b, int src) {
     const uint64_t f = *s.frame;
     const int64_t n = s.count[src];
     const int dst = src ^ 1;
     const uint64_t kn = key(s.seed, f, b, 3), ks = key(s.seed, f, b, 4), kj = key(s.seed, f, b, 5);
+    const uint64_t ku = key(s.seed, f, b + 1, 2);
+    const bool next = b + 1 < s.bounces;
     const unsigned lane = threadIdx.x & 31;
     for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = i0 + threadIdx.x;
@@ -165,6 +165,7 @@ __global__ void k_wf_advance(WfState s, int b, int src) {
             const int64_t j = base + __popc(mask & ((1u << lane) - 1u));
             for (int r = 0; r < 3; ++r) s.pos[dst][r * s.P + j] = x[r];
             s.pid[dst][j] = p;
+            if (next) write_uniforms(s, ku, j, (uint64_t)p);
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(s.queries, (unsigned long long)n);
@@ -210,7 +211,6 @@ npm_status enqueue_frame(npm_wavefront* w, cudaStream_t st) {
     for (int b = 0; b < s.bounces; ++b) {
         const int src = b & 1;
         k_wf_clear<<<1, 32, 0, st>>>(s, src ^ 1);
-        k_wf_uniforms<<<g, 256, 0, st>>>(s, b, src);
         npm::QueryBatch qb;
         memset(&qb, 0, sizeof(qb));
         qb.nseg = 1;
