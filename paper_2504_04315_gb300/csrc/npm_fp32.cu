@@ -32,8 +32,8 @@ constexpr unsigned kFull = 0xffffffffu;
 __host__ __device__ constexpr int fwd_act_stride(int I) { return 16 * I + 4; }
 
 // Tile groups per CTA of that instance: the register file holds 4 groups at
-// 128 registers a thread, 5 at 96 (enough for the narrow instance only).
-__host__ __device__ constexpr int fwd_max_groups(int I) { return I <= 2 ? 5 : 4; }
+// 128 registers a thread, 6 at 80 (enough for the narrow instance only).
+__host__ __device__ constexpr int fwd_max_groups(int I) { return I <= 2 ? 6 : 4; }
 
 // ----------------------------------------------------------- tile GEMM
 
@@ -87,20 +87,39 @@ __device__ __forceinline__ void tile_gemm(int t, const float* in, int AS_rt, int
 #pragma unroll
         for (int i = 0; i < NP2; ++i) acc[j][i] = make_float2(0.0f, 0.0f);
     }
-    for (int k = 0; k < K; k += 4) {
-        float4 a[8];
+    if constexpr (NI <= 2) {
+        // Narrow layers: the K step's 4 x NI weights stay in registers and the
+        // activation rows stream through one at a time (fewer live registers,
+        // so more tile groups fit).
+        for (int k = 0; k < K; k += 4) {
+            float w[4][NI];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) a[j] = *reinterpret_cast<const float4*>(in + (qg + 8 * j) * AS + k);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            float w[NI];
-            load_w<NI>(WT + (k + kk) * NP + g * NI, w);
+            for (int kk = 0; kk < 4; ++kk) load_w<NI>(WT + (k + kk) * NP + g * NI, w[kk]);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const float av = kk == 0 ? a[j].x : kk == 1 ? a[j].y : kk == 2 ? a[j].z : a[j].w;
-                if constexpr (NI == 1) {
-                    acc1[j] = fmaf(av, w[0], acc1[j]);
-                } else {
+                const float4 a = *reinterpret_cast<const float4*>(in + (qg + 8 * j) * AS + k);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const float av = kk == 0 ? a.x : kk == 1 ? a.y : kk == 2 ? a.z : a.w;
+                    if constexpr (NI == 1)
+                        acc1[j] = fmaf(av, w[kk][0], acc1[j]);
+                    else
+                        acc[j][0] = __ffma2_rn(make_float2(av, av), make_float2(w[kk][0], w[kk][1]), acc[j][0]);
+                }
+            }
+        }
+    } else {
+        for (int k = 0; k < K; k += 4) {
+            float4 a[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) a[j] = *reinterpret_cast<const float4*>(in + (qg + 8 * j) * AS + k);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                float w[NI];
+                load_w<NI>(WT + (k + kk) * NP + g * NI, w);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float av = kk == 0 ? a[j].x : kk == 1 ? a[j].y : kk == 2 ? a[j].z : a[j].w;
                     const float2 aa = make_float2(av, av);
 #pragma unroll
                     for (int i = 0; i < NP2; ++i)
@@ -461,6 +480,27 @@ __global__ void __launch_bounds__(fwd_max_groups(NIMAX) * kNT, 1) k_forward_fp32
         const int64_t base = (tile - S.tile0) * kTQ;
         encode_tile(t, cfg, grid, base, n, S.ld, S.pos, S.aux, act, AS);
         group_sync(group);
+        // Bring the next tile's positions and this tile's uniforms into L2
+        // while the MLP runs (one thread per 32 consecutive queries).
+        if ((t & 31) == 0 && t < 2 * kTQ) {
+            const int row = t >> 5;  // 0..3: u rows 0..2 of this tile, pos of the next
+            if (row < 3) {
+                const int64_t jj = base + (t & (kTQ - 1));
+                if (jj < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(S.uin + row * S.ld + jj));
+            } else {
+                const int64_t nt = tile + (int64_t)gridDim.x * G;
+                if (nt < total) {
+                    int s2 = s;
+                    while (s2 + 1 < qb.nseg && nt >= qb.seg[s2 + 1].tile0) ++s2;
+                    const QuerySeg& S2 = qb.seg[s2];
+                    const int64_t b2 = (nt - S2.tile0) * kTQ;
+                    for (int r = 0; r < 3; ++r) {
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(S2.pos + r * S2.ld + b2));
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(S2.pos + r * S2.ld + b2 + 32));
+                    }
+                }
+            }
+        }
         for (int l = 0; l < cfg.n_layers; ++l) {
             const bool last = l == cfg.n_layers - 1;
             layer<NIMAX, AS, true>(t, act, AS, cfg.widths[l], sW + cfg.off_fwd[l], cfg.np_fwd[l], act,

@@ -460,7 +460,9 @@ __device__ __forceinline__ void tc_decode(const TcCfg& tc, const float (&raw)[4 
 
 // --------------------------------------------------------------- kernel
 
-template <int KMAX, bool F2>
+// NL > 0: the network has exactly NL layers (loops over layers and output
+// chunks unrolled at compile time); NL = 0: any layer count.
+template <int KMAX, bool F2, int NL>
 __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? 6 : 1) k_forward_tc(const __grid_constant__ TcCfg tc,
                                                          const __half* __restrict__ grid_h,
                                                          const uint8_t* __restrict__ wblob,
@@ -523,7 +525,9 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? 6 : 1) k_forwar
     const uint32_t sA_addr = smem_u32(sA), sA0_addr = smem_u32(sA0);
     const uint32_t sW_addr = smem_u32(sW);
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    const int L = tc.base.n_layers;
+    const int L = NL > 0 ? NL : tc.base.n_layers;
+    constexpr int kUnrollL = NL > 0 ? NL : 1;
+    constexpr int kUnrollC = NL > 0 ? NPM_MAX_WIDTH / 16 : 1;
 
     int64_t ntiles = qb.total_tiles, n0 = qb.seg[0].n;
     if (qb.n_dev) {
@@ -544,6 +548,7 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? 6 : 1) k_forwar
         tc_fence_before();
         __syncthreads();
         uint32_t raw[4 * KMAX / 16][16];
+#pragma unroll kUnrollL
         for (int l = 0; l < L; ++l) {
             const TcLayer& ly = tc.layer[l];
             if (t == 0) {
@@ -572,6 +577,7 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? 6 : 1) k_forwar
             tc_fence_after();
             if (l < L - 1) {
                 const int kp_next = tc.layer[l + 1].Kp;
+#pragma unroll kUnrollC
                 for (int c0 = 0; c0 < ly.Np; c0 += 16) {
                     uint32_t r[16];
                     tmem_ld16(tmem + lane_base + (uint32_t)c0, r);
@@ -1200,10 +1206,10 @@ cudaError_t tc_refresh_weights(npm_handle* h, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int KMAX, bool F2>
+template <int KMAX, bool F2, int NL>
 static cudaError_t launch_tc(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStream_t st) {
     TcState* s = h->tc;
-    auto kern = k_forward_tc<KMAX, F2>;
+    auto kern = k_forward_tc<KMAX, F2, NL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem);
     if (e != cudaSuccess) return e;
     // CTAs per SM from registers and tensor memory; then carve out just the
@@ -1282,11 +1288,17 @@ cudaError_t tc_train(npm_handle* h, int64_t n, int64_t ld, const float* pos, con
 }
 
 cudaError_t tc_query_batch(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStream_t st) {
-    const int K = h->cfg.K;
+    const int K = h->cfg.K, L = h->cfg.n_layers;
     const bool f2 = h->cfg.feat_per_level == 2;
-    if (K <= 4) return f2 ? launch_tc<4, true>(h, qb, max_n, st) : launch_tc<4, false>(h, qb, max_n, st);
-    if (K <= 8) return f2 ? launch_tc<8, true>(h, qb, max_n, st) : launch_tc<8, false>(h, qb, max_n, st);
-    return f2 ? launch_tc<16, true>(h, qb, max_n, st) : launch_tc<16, false>(h, qb, max_n, st);
+    // The small three-layer K <= 4 networks get an instance with the layer
+    // loop unrolled (measured faster there; on the four-layer paper-shaped
+    // networks unrolling was slower).
+    if (K <= 4) {
+        if (L == 3 && !f2) return launch_tc<4, false, 3>(h, qb, max_n, st);
+        return f2 ? launch_tc<4, true, 0>(h, qb, max_n, st) : launch_tc<4, false, 0>(h, qb, max_n, st);
+    }
+    if (K <= 8) return f2 ? launch_tc<8, true, 0>(h, qb, max_n, st) : launch_tc<8, false, 0>(h, qb, max_n, st);
+    return f2 ? launch_tc<16, true, 0>(h, qb, max_n, st) : launch_tc<16, false, 0>(h, qb, max_n, st);
 }
 
 npm_status tc_query(npm_handle* h, int64_t n, int64_t ld, const float* pos, const float* aux,

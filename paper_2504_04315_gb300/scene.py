@@ -40,23 +40,36 @@ def radiance(product: bool, pos, aux, dirs, noise_seed: int = 0, clean: bool = T
     return c, z
 
 
-def online_step(model: NPM, seed: int, n: int, uniform_frac: float = 0.5, stream=None):
-    """One online training step on n fresh samples; returns the loss tensor."""
+def _guide_input(pos, fixed_position: Optional[float]):
+    """The positions the guide sees: the vertices', or one constant point for
+    every vertex (a position-independent guide: a single mixture for the
+    whole scene)."""
+    return pos if fixed_position is None else _torch().full_like(pos, float(fixed_position))
+
+
+def online_step(model: NPM, seed: int, n: int, uniform_frac: float = 0.5,
+                fixed_position: Optional[float] = None, stream=None):
+    """One online training step on n fresh samples; returns the loss tensor.
+    With fixed_position the guide is queried and trained at that constant
+    point, while the target is evaluated at the real vertices."""
     product = model.mode == PRODUCT
     pos, aux, u = generate(seed, n, product, urows=4, stream=stream)
-    d, p, _ = model.query_sample(pos, u, aux, uniform_frac=uniform_frac, stream=stream)
+    gpos = _guide_input(pos, fixed_position)
+    d, p, _ = model.query_sample(gpos, u, aux, uniform_frac=uniform_frac, stream=stream)
     _, noisy = radiance(product, pos, aux, d, noise_seed=seed, clean=False, stream=stream)
-    return model.train_step(pos, d, noisy, p, aux, stream=stream)
+    return model.train_step(gpos, d, noisy, p, aux, stream=stream)
 
 
 def relative_variance(model: NPM, product: bool, seed: int, n: int, uniform: bool = False,
-                      stream=None):
+                      fixed_position: Optional[float] = None, stream=None):
     """Relative variance var(I) / mean(I)^2 of the one-sample estimator
     I = target(x, w) / pdf(w | x) over n vertices, with w drawn from the
     model's guide, or uniformly on the sphere (uniform=True, the "no guide"
-    baseline: the same kernel with uniform_frac = 1)."""
+    baseline: the same kernel with uniform_frac = 1). fixed_position: the
+    guide sees that constant point (see online_step)."""
     pos, aux, u = generate(seed, n, product, urows=4, stream=stream)
-    d, p, _ = model.query_sample(pos, u, aux, uniform_frac=1.0 if uniform else 0.0, stream=stream)
+    d, p, _ = model.query_sample(_guide_input(pos, fixed_position), u, aux,
+                                 uniform_frac=1.0 if uniform else 0.0, stream=stream)
     clean, _ = radiance(product, pos, aux, d, noisy=False, stream=stream)
     est = clean.double() / p.double()
     return float(est.var() / est.mean() ** 2), float(est.mean())

@@ -67,11 +67,11 @@ def test_multistep_loss_curve_tracks_oracle():
     assert np.abs(gl - ol).max() <= 1e-3 * np.abs(ol).max(), np.abs(gl - ol).max()
 
 
-def _online(m, steps, n, seed0):
+def _online(m, steps, n, seed0, fixed_position=None):
     from paper_2504_04315_gb300 import scene
     losses = []
     for s in range(steps):
-        losses.append(scene.online_step(m, seed0 + s, n))
+        losses.append(scene.online_step(m, seed0 + s, n, fixed_position=fixed_position))
     return [float(x) for x in torch.stack(losses).cpu().numpy().ravel()]
 
 
@@ -94,6 +94,15 @@ def test_online_training_gains_over_uniform_radiance():
     assert rv_trained < 0.5 * rv_uniform
     assert rv_trained < 0.5 * rv_untrained
     assert np.mean(losses[-20:]) < np.mean(losses[:20])
+    # Position-independent guide: the same network and training, but every
+    # vertex is presented at one point, so it can only learn a single mixture
+    # for the whole scene. The spatially varying guide must beat it.
+    g = make_model(w, synth.init_params(w), 1 << 16)
+    _online(g, 1000, 1 << 16, 1000, fixed_position=0.5)
+    rv_global, _ = scene.relative_variance(g, False, 999, 1 << 16, fixed_position=0.5)
+    print(f"radiance: position-independent single mixture {rv_global:.3f}")
+    assert rv_global < rv_uniform
+    assert rv_trained < 0.7 * rv_global
 
 
 def test_product_workload_200_steps():
