@@ -388,6 +388,61 @@ def main():
                    "bounce_p50_ms": sv["bounce_p50_ms"], "bounce_p99_ms": sv["bounce_p99_ms"],
                    "frame_ms_mean": sv["frame_ms_mean"], "train_ms_mean": sv["train_ms_mean"]}
 
+    # Continuous batching through the request server: 4 client threads, each
+    # submitting wavefront-shaped query requests (2^18 * 0.7^b queries for
+    # bounces b = 0..7, host buffers) and one 2^16-sample training request
+    # per round; throughput and submit-to-result latency on the host.
+    server = None
+    if not args.no_extras:
+        import threading
+        sw = synth.TINY_BF16
+        base_n, rounds, clients = 1 << 18, 6, 4
+        sizes = [max(1, int(base_n * 0.7 ** b)) for b in range(8)]
+        msrv = npm.NPM(npm.config_from(sw, max_batch=base_n))
+        msrv.set_params(synth.random_params(sw, 3))
+
+        def client_bufs(c):
+            bufs = []
+            for b, nq in enumerate(sizes):
+                pos_h = torch.from_numpy(synth.positions(300 + 10 * c + b, nq)).pin_memory()
+                u_h = torch.from_numpy(synth.sample_uniforms(300 + 10 * c + b, nq)).pin_memory()
+                bufs.append((pos_h, u_h, torch.empty((3, nq)).pin_memory(), torch.empty((nq,)).pin_memory()))
+            tb = synth.train_batch_uniform(sw, 1 << 16, seed=400 + c)
+            tr = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                  for a in (tb.pos, tb.dir, tb.radiance, tb.pdf)]
+            return bufs, tr
+
+        cb = [client_bufs(c) for c in range(clients)]
+        with npm.Server(msrv, 4 * base_n) as srv:
+            def client(c, nrounds):
+                bufs, tr = cb[c]
+                for _ in range(nrounds):
+                    tk = [srv.submit_query(*r) for r in bufs]
+                    tk.append(srv.submit_train(*tr))
+                    for t in tk:
+                        srv.wait(t)
+
+            client(0, 1)  # warm-up
+            th = [threading.Thread(target=client, args=(c, rounds)) for c in range(clients)]
+            t0 = time.perf_counter()
+            for x in th:
+                x.start()
+            for x in th:
+                x.join()
+            wall = time.perf_counter() - t0
+            st = srv.stats()
+        msrv.close()
+        nq_total = clients * rounds * sum(sizes)
+        server = {"workload": f"{clients} client threads x {rounds} rounds of 8 query requests "
+                              f"(2^18 x 0.7^b queries, host buffers) + one 2^16-sample training "
+                              f"request; " + sw.name,
+                  "unit": "queries/s", "value": nq_total * world / wall,
+                  "train_samples_per_s": clients * rounds * (1 << 16) * world / wall,
+                  "request_latency_p50_ms": st["latency_p50_ms"],
+                  "request_latency_p99_ms": st["latency_p99_ms"],
+                  "launches": st["batches"], "max_requests_per_launch": st["max_requests_per_batch"],
+                  "pool_peak_queries": st["pool_peak_used"]}
+
     # Training throughput (samples/s): one npm_train_step per step on the
     # product-mode workload's batch (2^19): split BF16 on tensor cores (the
     # workload's precision) and the FP32 kernels.
@@ -472,6 +527,7 @@ def main():
         "train": train,
         "reduced_precision": reduced,
         "serving": serving,
+        "server": server,
         "peaks_source": pk_src,
         "unit_peaks": unit_peaks,
     }
