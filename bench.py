@@ -396,7 +396,7 @@ def main():
     if not args.no_extras:
         import threading
         sw = synth.TINY_BF16
-        base_n, rounds, clients = 1 << 18, 6, 4
+        base_n, rounds, clients = 1 << 18, 40, 4
         sizes = [max(1, int(base_n * 0.7 ** b)) for b in range(8)]
         msrv = npm.NPM(npm.config_from(sw, max_batch=base_n))
         msrv.set_params(synth.random_params(sw, 3))

@@ -232,13 +232,11 @@ __device__ __forceinline__ float vmf_eval(const Lobe& L, float cn, float wx, flo
 // < 3e-8 relative), by the hardware exponential above; the lobe value by the
 // hardware exponential of kappa (mu.w - 1) <= 0.
 __device__ __forceinline__ float vmf_scaled_norm_fast(float k) {
-    float em;
-    if (k < 0.05f)
-        em = k * (2.0f + k * (-2.0f + k * (4.0f / 3.0f + k * (-2.0f / 3.0f + k * (4.0f / 15.0f)))));
-    else
-        em = 1.0f - __expf(-2.0f * k);
-    if (k < 1e-6f) return (1.0f + k) * kInv4Pi;
-    return __fdividef(k, 2.0f * kPi * em);
+    // Both forms are evaluated and selected (no divergent branch per lobe).
+    const float series = k * (2.0f + k * (-2.0f + k * (4.0f / 3.0f + k * (-2.0f / 3.0f + k * (4.0f / 15.0f)))));
+    const float em = k < 0.05f ? series : 1.0f - __expf(-2.0f * k);
+    const float c = __fdividef(k, 2.0f * kPi * em);
+    return k < 1e-6f ? (1.0f + k) * kInv4Pi : c;
 }
 
 __device__ __forceinline__ float vmf_eval_fast(const Lobe& L, float cn, float wx, float wy, float wz) {

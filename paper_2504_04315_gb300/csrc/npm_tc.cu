@@ -370,14 +370,15 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
 
 // --------------------------------------------------------------- decode
 
-template <int KMAX>
+// KEXACT: the model has exactly KMAX lobes (no per-lobe bound checks).
+template <int KMAX, bool KEXACT>
 __device__ __forceinline__ void tc_decode(const TcCfg& tc, const float (&raw)[4 * KMAX], int64_t j,
                                           bool valid, int64_t ld, const float* __restrict__ uin,
                                           float ufrac, bool sample, float* __restrict__ dir_out,
                                           float* __restrict__ pdf_out,
                                           float* __restrict__ mix_out) {
     const DevCfg& cfg = tc.base;
-    const int K = cfg.K;
+    const int K = KEXACT ? KMAX : cfg.K;
     Lobe lob[KMAX];
     float cn[KMAX];
     float mx = -INFINITY;
@@ -460,8 +461,9 @@ __device__ __forceinline__ void tc_decode(const TcCfg& tc, const float (&raw)[4 
 
 // --------------------------------------------------------------- kernel
 
-// NL > 0: the network has exactly NL layers (loops over layers and output
-// chunks unrolled at compile time); NL = 0: any layer count.
+// NL > 0: the network has exactly NL layers and KMAX lobes (loops over
+// layers, output chunks and lobes unrolled at compile time); NL = 0: any
+// layer count and K <= KMAX.
 template <int KMAX, bool F2, int NL>
 __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? 6 : 1) k_forward_tc(const __grid_constant__ TcCfg tc,
                                                          const __half* __restrict__ grid_h,
@@ -607,7 +609,7 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? 6 : 1) k_forwar
         for (int c = 0; c < 4 * KMAX / 16; ++c)
 #pragma unroll
             for (int i = 0; i < 16; ++i) rawf[c * 16 + i] = __uint_as_float(raw[c][i]);
-        tc_decode<KMAX>(tc, rawf, j, valid, ld, S.uin, S.ufrac, qb.sample != 0, S.dir, S.pdf, S.mix);
+        tc_decode<KMAX, (NL > 0)>(tc, rawf, j, valid, ld, S.uin, S.ufrac, qb.sample != 0, S.dir, S.pdf, S.mix);
     }
     if (!ok && t == 0) atomicOr(status, kStatusTimeout);
     tc_fence_before();
@@ -1290,11 +1292,11 @@ cudaError_t tc_train(npm_handle* h, int64_t n, int64_t ld, const float* pos, con
 cudaError_t tc_query_batch(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStream_t st) {
     const int K = h->cfg.K, L = h->cfg.n_layers;
     const bool f2 = h->cfg.feat_per_level == 2;
-    // The small three-layer K <= 4 networks get an instance with the layer
-    // loop unrolled (measured faster there; on the four-layer paper-shaped
-    // networks unrolling was slower).
+    // The small three-layer four-lobe networks get an instance with the layer
+    // and lobe loops unrolled (measured faster there; on the four-layer
+    // paper-shaped networks unrolling was slower).
     if (K <= 4) {
-        if (L == 3 && !f2) return launch_tc<4, false, 3>(h, qb, max_n, st);
+        if (L == 3 && K == 4 && !f2) return launch_tc<4, false, 3>(h, qb, max_n, st);
         return f2 ? launch_tc<4, true, 0>(h, qb, max_n, st) : launch_tc<4, false, 0>(h, qb, max_n, st);
     }
     if (K <= 8) return f2 ? launch_tc<8, true, 0>(h, qb, max_n, st) : launch_tc<8, false, 0>(h, qb, max_n, st);

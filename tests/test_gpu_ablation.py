@@ -34,13 +34,19 @@ def test_multiresolution_encoding_beats_monolithic():
     rv = {}
     for name, w in encs.items():
         m = make_model(w, synth.init_params(w), n)
+        # Online training feeds on its own samples, and the grid gradients are
+        # sums of atomic adds in run-dependent order, so a single evaluation
+        # fluctuates from run to run: average the last three checkpoints.
+        evals = []
         for s in range(steps):
             scene.online_step(m, 7000 + s, n)
-        rv[name] = scene.relative_variance(m, False, 999, n)[0]
+            if s + 1 in (800, 900, 1000):
+                evals.append(scene.relative_variance(m, False, 999, n)[0])
+        rv[name] = sum(evals) / len(evals)
         m.close()
     rv_uniform = scene.relative_variance(make_model(encs["monolithic"], synth.init_params(encs["monolithic"]), n),
                                          False, 999, n, uniform=True)[0]
-    print("encoding ablation, relative variance after %d steps: uniform %.3f, " % (steps, rv_uniform)
+    print("encoding ablation, relative variance (mean of steps 800/900/1000): uniform %.3f, " % rv_uniform
           + ", ".join(f"{k} {v:.3f}" for k, v in rv.items()))
     assert all(v < rv_uniform for v in rv.values())
     assert rv["multi-resolution"] < rv["monolithic"]
