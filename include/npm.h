@@ -437,6 +437,7 @@ const char* npm_last_error(void);
  *                       64 MiB buffer resident in L2, bytes of sectors/s
  *   l2_atomic_gops      random FP32 atomic adds (no return) into that buffer
  *   l2_atomic_v2_gops   the same with two-wide FP32 vector atomic adds
+ *   l2_atomic_v4_gops   the same with four-wide FP32 vector atomic adds
  *   sm_count, max_sm_clock_mhz  the device's SM count and rated clock
  * Allocates and frees 64 MiB of device memory; runs a few milliseconds of
  * kernels on `stream` and synchronises it. Not for use inside a capture.
@@ -444,7 +445,7 @@ const char* npm_last_error(void);
  */
 typedef struct npm_unit_peaks {
     double fp32_fma_tflops, fp32_fma_scalar_tflops, mufu_gops, l2_sector_read_gbs, l2_atomic_gops,
-        l2_atomic_v2_gops;
+        l2_atomic_v2_gops, l2_atomic_v4_gops;
     int sm_count;
     double max_sm_clock_mhz;
 } npm_unit_peaks;

@@ -62,7 +62,7 @@ class NpmUnitPeaks(C.Structure):
         ("fp32_fma_tflops", C.c_double), ("fp32_fma_scalar_tflops", C.c_double),
         ("mufu_gops", C.c_double),
         ("l2_sector_read_gbs", C.c_double), ("l2_atomic_gops", C.c_double),
-        ("l2_atomic_v2_gops", C.c_double), ("sm_count", C.c_int),
+        ("l2_atomic_v2_gops", C.c_double), ("l2_atomic_v4_gops", C.c_double), ("sm_count", C.c_int),
         ("max_sm_clock_mhz", C.c_double),
     ]
 

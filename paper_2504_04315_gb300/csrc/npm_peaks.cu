@@ -1,7 +1,7 @@
 // npm_peaks.cu -- measured throughput of the units the hot path leans on:
 // FP32 FMA (packed two-lane and scalar), the MUFU exponential, random
-// 32-byte sector reads from L2, and random FP32 (scalar and 2-wide vector)
-// atomic adds into L2. The roofline
+// 32-byte sector reads from L2, and random FP32 (scalar, 2- and 4-wide
+// vector) atomic adds into L2. The roofline
 // of each kernel is the minimum over its HBM, L2, tensor and ALU/MUFU bounds;
 // HBM and tensor peaks are copy and GEMM measurements, these are the rest.
 //
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kThreads) k_l2_read(const float* __restrict__ 
 }
 
 // Random atomic adds without return (reductions in L2): W = 1 scalar,
-// W = 2 two-wide vector.
+// W = 2 and 4 vector.
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_l2_atomic(float* __restrict__ buf, int iters) {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -100,8 +100,10 @@ __global__ void __launch_bounds__(kThreads) k_l2_atomic(float* __restrict__ buf,
             const uint32_t slot = hash32(tid * 0x9E3779B9u + (uint32_t)(it * 8 + i)) & (kBufFloats / 8 - 1);
             if constexpr (W == 1)
                 atomicAdd(buf + slot * 8, 1.0f);
-            else
+            else if constexpr (W == 2)
                 atomicAdd(reinterpret_cast<float2*>(buf + slot * 8), make_float2(1.0f, 1.0f));
+            else
+                atomicAdd(reinterpret_cast<float4*>(buf + slot * 8), make_float4(1.0f, 1.0f, 1.0f, 1.0f));
         }
     }
 }
@@ -152,6 +154,7 @@ extern "C" npm_status npm_measure_unit_peaks(npm_unit_peaks* out, void* stream) 
     const float ms_rd = best_ms([&] { k_l2_read<<<blocks, kThreads, 0, st>>>(buf, sink, mem_iters); }, st, e0, e1, 3);
     const float ms_at1 = best_ms([&] { k_l2_atomic<1><<<blocks, kThreads, 0, st>>>(buf, mem_iters); }, st, e0, e1, 3);
     const float ms_at2 = best_ms([&] { k_l2_atomic<2><<<blocks, kThreads, 0, st>>>(buf, mem_iters); }, st, e0, e1, 3);
+    const float ms_at4 = best_ms([&] { k_l2_atomic<4><<<blocks, kThreads, 0, st>>>(buf, mem_iters); }, st, e0, e1, 3);
     const cudaError_t err = cudaGetLastError();
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -166,6 +169,7 @@ extern "C" npm_status npm_measure_unit_peaks(npm_unit_peaks* out, void* stream) 
     out->l2_sector_read_gbs = accesses * 32.0 / (ms_rd * 1e-3) / 1e9;
     out->l2_atomic_gops = accesses / (ms_at1 * 1e-3) / 1e9;
     out->l2_atomic_v2_gops = accesses / (ms_at2 * 1e-3) / 1e9;
+    out->l2_atomic_v4_gops = accesses / (ms_at4 * 1e-3) / 1e9;
     out->sm_count = sms;
     out->max_sm_clock_mhz = clk_khz / 1000.0;
     return NPM_OK;
