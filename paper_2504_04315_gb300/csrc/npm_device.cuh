@@ -109,6 +109,23 @@ __device__ __forceinline__ void corners8(const DevCfg& cfg, int l, const Cell& c
     corner_w8(cl, w);
 }
 
+// Grid-gradient scatter of two x-adjacent corners (entries a, b of a level
+// starting at entry level_off, 2 features each; gl points at the level):
+// when the two entries form one 16-byte aligned pair, one 4-wide atomic add
+// serves both (the L2 atomic units are limited by operations, not bytes).
+__device__ __forceinline__ void scatter_pair2(float* gl, uint32_t level_off, uint32_t a, uint32_t b, float wa,
+                                              float wb, float d0, float d1) {
+    const uint32_t lo = a < b ? a : b;
+    if ((a > b ? a - b : b - a) == 1u && ((level_off + lo) & 1u) == 0u) {
+        const float4 v = a < b ? make_float4(wa * d0, wa * d1, wb * d0, wb * d1)
+                               : make_float4(wb * d0, wb * d1, wa * d0, wa * d1);
+        atomicAdd(reinterpret_cast<float4*>(gl + (size_t)lo * 2), v);
+    } else {
+        atomicAdd(reinterpret_cast<float2*>(gl + (size_t)a * 2), make_float2(wa * d0, wa * d1));
+        atomicAdd(reinterpret_cast<float2*>(gl + (size_t)b * 2), make_float2(wb * d0, wb * d1));
+    }
+}
+
 // ------------------------------------------ spherical harmonics (Sec. 4.3)
 
 // Real orthonormal SH, bands 0..3 (16 values), in the order

@@ -658,13 +658,17 @@ __device__ __forceinline__ void grid_scatter(const DevCfg& cfg, const float* den
         uint32_t idx[8];
         float ws[8];
         corners8(cfg, l, cl, idx, ws);
+        if (F == 2) {
+#pragma unroll
+            for (int c = 0; c < 8; c += 2)
+                scatter_pair2(gl, cfg.level_off[l], idx[c], idx[c + 1], ws[c], ws[c + 1], dg[0], dg[1]);
+            continue;
+        }
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const float w = ws[c];
             float* e = gl + (size_t)idx[c] * F;
-            if (F == 2) {
-                atomicAdd(reinterpret_cast<float2*>(e), make_float2(w * dg[0], w * dg[1]));
-            } else if (F == 4) {
+            if (F == 4) {
                 atomicAdd(reinterpret_cast<float4*>(e),
                           make_float4(w * dg[0], w * dg[1], w * dg[2], w * dg[3]));
             } else {

@@ -791,21 +791,9 @@ __device__ __forceinline__ void scatter_levels(const DevCfg& cfg, float* __restr
                 if constexpr (FF == 1) {
                     atomicAdd(e, wc * dg[q]);
                 } else if constexpr (FF == 2) {
-                    // Corners c and c + 1 (along x) often sit in one 16-byte
-                    // aligned pair of entries: then one 4-wide atomic add
-                    // serves both (the L2 atomic units are limited by
-                    // operations, not bytes).
-                    if (c & 1) continue;
-                    const uint32_t a = idx[c], b = idx[c + 1], lo = a < b ? a : b;
-                    const float d0 = dg[2 * q], d1 = dg[2 * q + 1], wa = ws[c], wb = ws[c + 1];
-                    if ((a > b ? a - b : b - a) == 1u && ((cfg.level_off[l] + lo) & 1u) == 0u) {
-                        const float4 v = a < b ? make_float4(wa * d0, wa * d1, wb * d0, wb * d1)
-                                               : make_float4(wb * d0, wb * d1, wa * d0, wa * d1);
-                        atomicAdd(reinterpret_cast<float4*>(gl + (size_t)lo * 2), v);
-                    } else {
-                        atomicAdd(reinterpret_cast<float2*>(gl + (size_t)a * 2), make_float2(wa * d0, wa * d1));
-                        atomicAdd(reinterpret_cast<float2*>(gl + (size_t)b * 2), make_float2(wb * d0, wb * d1));
-                    }
+                    if (c & 1) continue;  // corners c, c + 1 (along x) together
+                    scatter_pair2(gl, cfg.level_off[l], idx[c], idx[c + 1], ws[c], ws[c + 1], dg[2 * q],
+                                  dg[2 * q + 1]);
                 } else {
 #pragma unroll
                     for (int f = 0; f < FF; f += 4)
