@@ -4,6 +4,7 @@
 // mixture density (Eq. 3-4) and vMF sampling (Sec. 5.3).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -107,6 +108,41 @@ __device__ __forceinline__ void corners8(const DevCfg& cfg, int l, const Cell& c
                                          float (&w)[8]) {
     corner_idx8(cfg, l, cl, idx);
     corner_w8(cl, w);
+}
+
+// Features of two x-adjacent corners (entries a, b of a 2-feature level
+// starting at entry level_off; gl points at the level): one 16-byte load
+// (FP32) or 8-byte load (FP16) when the two entries form an aligned pair,
+// else one load each. Random gathers cost the L1 a wavefront per lane and
+// load, so the paired lanes halve their share.
+__device__ __forceinline__ void gather_pair2(const float* gl, uint32_t level_off, uint32_t a, uint32_t b,
+                                             float2& va, float2& vb) {
+    const uint32_t lo = a < b ? a : b;
+    if ((a > b ? a - b : b - a) == 1u && ((level_off + lo) & 1u) == 0u) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(gl + (size_t)lo * 2));
+        const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
+        va = a < b ? v0 : v1;
+        vb = a < b ? v1 : v0;
+    } else {
+        va = __ldg(reinterpret_cast<const float2*>(gl) + a);
+        vb = __ldg(reinterpret_cast<const float2*>(gl) + b);
+    }
+}
+__device__ __forceinline__ void gather_pair2(const __half* gl, uint32_t level_off, uint32_t a, uint32_t b,
+                                             float2& va, float2& vb) {
+    const uint32_t lo = a < b ? a : b;
+    if ((a > b ? a - b : b - a) == 1u && ((level_off + lo) & 1u) == 0u) {
+        const uint2 raw = __ldg(reinterpret_cast<const uint2*>(gl + (size_t)lo * 2));
+        const float2 v0 = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
+        const float2 v1 = __half22float2(*reinterpret_cast<const __half2*>(&raw.y));
+        va = a < b ? v0 : v1;
+        vb = a < b ? v1 : v0;
+    } else {
+        const unsigned int ra = __ldg(reinterpret_cast<const unsigned int*>(gl) + a);
+        const unsigned int rb = __ldg(reinterpret_cast<const unsigned int*>(gl) + b);
+        va = __half22float2(*reinterpret_cast<const __half2*>(&ra));
+        vb = __half22float2(*reinterpret_cast<const __half2*>(&rb));
+    }
 }
 
 // Grid-gradient scatter of two x-adjacent corners (entries a, b of a level

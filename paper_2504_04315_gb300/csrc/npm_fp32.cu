@@ -184,7 +184,7 @@ __device__ __forceinline__ void gather_level(const DevCfg& cfg, const float* __r
     if (F == 2) {
         float2 v[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) v[c] = __ldg(reinterpret_cast<const float2*>(gl) + idx[c]);
+        for (int c = 0; c < 8; c += 2) gather_pair2(gl, cfg.level_off[l], idx[c], idx[c + 1], v[c], v[c + 1]);
         corner_w8(cl, w);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {

@@ -269,9 +269,11 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
             const GT* g1 = grid_h + (size_t)cfg.level_off[l + 1] * 2;
             float2 v0[8], v1[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                v0[c] = load_feat2(g0, corner_idx1(cfg, l, c0, c));
-                v1[c] = load_feat2(g1, corner_idx1(cfg, l + 1, c1, c));
+            for (int c = 0; c < 8; c += 2) {
+                gather_pair2(g0, cfg.level_off[l], corner_idx1(cfg, l, c0, c), corner_idx1(cfg, l, c0, c + 1),
+                             v0[c], v0[c + 1]);
+                gather_pair2(g1, cfg.level_off[l + 1], corner_idx1(cfg, l + 1, c1, c),
+                             corner_idx1(cfg, l + 1, c1, c + 1), v1[c], v1[c + 1]);
             }
             float w0s[8], w1s[8];
             corner_w8(c0, w0s);
@@ -465,7 +467,7 @@ __device__ __forceinline__ void tc_decode(const TcCfg& tc, const float (&raw)[4 
 // layers, output chunks and lobes unrolled at compile time); NL = 0: any
 // layer count and K <= KMAX.
 template <int KMAX, bool F2, int NL>
-__global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? 6 : 1) k_forward_tc(const __grid_constant__ TcCfg tc,
+__global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? 6 : (KMAX == 8 ? 3 : 1)) k_forward_tc(const __grid_constant__ TcCfg tc,
                                                          const __half* __restrict__ grid_h,
                                                          const uint8_t* __restrict__ wblob,
                                                          const __grid_constant__ QueryBatch qb,
