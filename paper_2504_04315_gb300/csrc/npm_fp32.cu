@@ -217,6 +217,9 @@ __device__ __forceinline__ void gather_level(const DevCfg& cfg, const float* __r
 
 // Fills act[q][0 .. widths[0]) for the tile's 64 queries; local thread t
 // handles query t % 64 and every other level (two levels in flight).
+// FOUR: 2-feature grids keep four levels' loads in flight (registers the
+// wide instances have to spare).
+template <bool FOUR>
 __device__ __forceinline__ void encode_tile(int t, const DevCfg& cfg, const float* __restrict__ grid,
                                             int64_t base, int64_t n, int64_t ld,
                                             const float* __restrict__ pos,
@@ -233,6 +236,36 @@ __device__ __forceinline__ void encode_tile(int t, const DevCfg& cfg, const floa
     float* row = act + q * AS;
     const int F = cfg.feat;
     int l = part;
+    if (FOUR && F == 2) {
+        // Four levels' corner loads in flight (levels l, l+2, l+4, l+6).
+        for (; l + 6 < cfg.n_levels; l += 8) {
+            Cell cs[4];
+            uint32_t idx[4][8];
+            float2 v[4][8];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                cs[r] = make_cell(x, y, z, cfg.level_res[l + 2 * r]);
+                corner_idx8(cfg, l + 2 * r, cs[r], idx[r]);
+                const float* gr = grid + (size_t)cfg.level_off[l + 2 * r] * 2;
+#pragma unroll
+                for (int c = 0; c < 8; c += 2)
+                    gather_pair2(gr, cfg.level_off[l + 2 * r], idx[r][c], idx[r][c + 1], v[r][c], v[r][c + 1]);
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                float w[8];
+                corner_w8(cs[r], w);
+                float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    a0 = fmaf(w[c], v[r][c].x, a0);
+                    a1 = fmaf(w[c], v[r][c].y, a1);
+                }
+                row[(l + 2 * r) * 2] = a0;
+                row[(l + 2 * r) * 2 + 1] = a1;
+            }
+        }
+    }
     for (; l + 2 < cfg.n_levels; l += 4) {
         const Cell c0 = make_cell(x, y, z, cfg.level_res[l]);
         const Cell c1 = make_cell(x, y, z, cfg.level_res[l + 2]);
@@ -478,7 +511,7 @@ __global__ void __launch_bounds__(fwd_max_groups(NIMAX) * kNT, 1) k_forward_fp32
         const QuerySeg& S = qb.seg[s];
         const int64_t n = (s == 0 && qb.n_dev) ? n0 : S.n;
         const int64_t base = (tile - S.tile0) * kTQ;
-        encode_tile(t, cfg, grid, base, n, S.ld, S.pos, S.aux, act, AS);
+        encode_tile<(NIMAX >= 4)>(t, cfg, grid, base, n, S.ld, S.pos, S.aux, act, AS);
         group_sync(group);
         // Bring the next tile's positions and this tile's uniforms into L2
         // while the MLP runs (one thread per 32 consecutive queries).
@@ -702,7 +735,7 @@ __global__ void __launch_bounds__(kNT) k_train_fp32(DevCfg cfg, const float* __r
     const int64_t ntiles = (n + kTQ - 1) / kTQ;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t base = tile * kTQ;
-        encode_tile(threadIdx.x, cfg, params, base, n, ld, pos, aux, buf(0), AS);
+        encode_tile<false>(threadIdx.x, cfg, params, base, n, ld, pos, aux, buf(0), AS);
         __syncthreads();
         for (int l = 0; l < L; ++l) {
             layer<8>(threadIdx.x, buf(l), AS, cfg.widths[l], sW + cfg.off_fwd[l], cfg.np_fwd[l],
