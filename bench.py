@@ -184,24 +184,43 @@ def run_reference(args, w, rank):
     pos = synth.positions(0, n)
     u = synth.sample_uniforms(0, n)
     aux = synth.aux_inputs(0, n) if w.mode == synth.PRODUCT else None
-    for _ in range(args.warmup):
-        oracle.query_sample(w, params, pos[:, :256], u[:, :256], aux[:, :256] if aux is not None else None)
+    train_mode = args.mode == "train"
+    if train_mode:
+        # One oracle training step (loss gradient + Adam) on n samples.
+        b = synth.train_batch_uniform(w, n, seed=0)
+        p64 = params.astype(np.float64)
+        m64, v64 = np.zeros_like(p64), np.zeros_like(p64)
+
+        def step(t, k):
+            _, g = oracle.train_grad(w, p64, b.pos[:, :k], b.dir[:, :k], b.radiance[:k], b.pdf[:k],
+                                     None if b.aux is None else b.aux[:, :k])
+            oracle.adam(p64, g, m64, v64, t, w.lr, w.beta1, w.beta2, w.eps)
+    else:
+        def step(t, k):
+            oracle.query_sample(w, params, pos[:, :k], u[:, :k], aux[:, :k] if aux is not None else None)
+    for i in range(args.warmup):
+        step(i + 1, 256)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.query_sample(w, params, pos, u, aux)
+    for i in range(args.steps):
+        step(args.warmup + i + 1, n)
     dt = time.perf_counter() - t0
     v = n * args.steps / dt
     cores = oracle.num_threads()
+    unit = "samples/s" if train_mode else "queries/s"
+    what = "training samples" if train_mode else "queries"
+    total = w.n_train if train_mode else w.n_query
     line = {
-        "impl": "reference", "metric": "guided queries/s (encode+decode+sample+pdf)",
-        "value": v, "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps,
+        "impl": "reference",
+        "metric": ("train samples/s (forward + backward + Adam)" if train_mode
+                   else "guided queries/s (encode+decode+sample+pdf)"),
+        "value": v, "unit": unit, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, ("samples_per_step" if train_mode else "queries_per_step"): n, "sample_of": w.n_query},
-        "cpu_baseline": {"value": v, "unit": "queries/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{n} queries per step of the {w.n_query}-query workload"},
-        "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 0},
+        "config": {"workload": w.name, ("samples_per_step" if train_mode else "queries_per_step"): n,
+                   "sample_of": total},
+        "cpu_baseline": {"value": v, "unit": unit, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} {what} per step of the {total}-{what[:-1]} workload"},
+        "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 

@@ -51,3 +51,21 @@ def test_single_rank_needs_no_process_group():
     import bench
     max_ms, value = bench.job_throughput(200.0, 100, 5, 1, None)
     assert max_ms == 200.0 and value == pytest.approx(2500.0)
+
+
+@pytest.mark.parametrize("extra", [[], ["--mode", "train", "--workload", "product_bf16"]])
+def test_reference_arm_prints_one_line(extra):
+    # The reference arm times the FP64 oracle on the host cores and prints the
+    # same JSON line shape as the main arm (no GPU involved).
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "3", "--ref-sample", "64"] + extra,
+                         capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["unit"] == line["e2e"]["unit"]
