@@ -414,7 +414,7 @@ npm_status npm_query_sample(npm_handle* h, int64_t n, const float* pos, const fl
     cudaStream_t st = (cudaStream_t)stream;
     if (h->tc) return npm::tc_query(h, n, ld, pos, aux, u, uniform_frac, true, dir_out, pdf_out, mix_out, st);
     NPM_CUDA(npm::launch_forward_fp32(h->dc, inf_params(h), inf_wfwd(h), n, ld, pos, aux, u, uniform_frac,
-                                      true, dir_out, pdf_out, mix_out, st),
+                                      true, dir_out, pdf_out, mix_out, st, status_word(h)),
              "query_sample launch");
     return NPM_OK;
 }
@@ -483,7 +483,7 @@ npm_status npm_eval_pdf(npm_handle* h, int64_t n, const float* pos, const float*
     cudaStream_t st = (cudaStream_t)stream;
     if (h->tc) return npm::tc_query(h, n, ld, pos, aux, dir, 0.0f, false, nullptr, pdf_out, nullptr, st);
     NPM_CUDA(npm::launch_forward_fp32(h->dc, inf_params(h), inf_wfwd(h), n, ld, pos, aux, dir, 0.0f, false,
-                                      nullptr, pdf_out, nullptr, st),
+                                      nullptr, pdf_out, nullptr, st, status_word(h)),
              "eval_pdf launch");
     return NPM_OK;
 }

@@ -1,6 +1,6 @@
 // npm_fp32.cu -- FP32 CUDA-core path of the NPM hot path.
 //
-// One persistent CTA of 128 threads walks 64-query tiles. Per tile:
+// Tile groups of 128 threads walk 64-query tiles. Per tile:
 //   encode  : 2 threads per query gather the 8 corners of every level and
 //             blend them (Sec. 5.1, Eq. 11); product mode appends the SH
 //             encodings and the roughness (Sec. 4.3).
@@ -10,6 +10,10 @@
 //   epilogue: 2 threads per query (lobes split in halves, combined with
 //             warp shuffles) map the raw outputs (Table 1), then sample and/or
 //             evaluate the mixture (Eq. 3-4).
+// The forward kernel for 64-wide networks splits these roles: one group
+// encodes for three groups that run the MLP and the epilogue
+// (k_forward_fp32_ws); other networks run every step in each group
+// (k_forward_fp32).
 // The training kernel recomputes the forward pass, forms the gradient of the
 // weighted log-likelihood in the log domain (Eq. 9), back-propagates through
 // the layers and scatters grid gradients with vector atomics.
@@ -67,15 +71,23 @@ __device__ __forceinline__ void load_w(const float* p, float (&w)[NI]) {
 // 1: ReLU, 2: keep where mask[q][n] > 0 (ReLU derivative), else 0.
 // AST > 0: the activation row stride is the compile-time AST (so row and
 // weight addresses are immediate offsets of two pointers); else AS_rt.
+// OST > 0: the output rows have the compile-time stride OST (the input may
+// then have another); else the input's.
 // INPLACE: out may equal in; the tile group (named barrier group + 1)
 // synchronises between the last read of in and the first store.
-template <int NI, int AST, bool INPLACE>
+template <int NI, int AST, bool INPLACE, int OST = 0>
 __device__ __forceinline__ void tile_gemm(int t, const float* in, int AS_rt, int K,
                                           const float* __restrict__ WT, float* out, int N, int mode,
                                           const float* __restrict__ mask, int group) {
     const int AS = AST > 0 ? AST : AS_rt;
+    const int OS = OST > 0 ? OST : AS;
     constexpr int NP = 16 * NI;
-    const int g = t & 15, qg = t >> 4;
+    // Thread t owns output group g (16 groups) and query group qg (8): a
+    // warp covers all 16 output groups and 2 query groups, lanes 2i and
+    // 2i + 1 sharing output group i. Lanes that read the same shared-memory
+    // vector are adjacent, which keeps a warp's 16-byte shared loads at two
+    // wavefronts (sharing between strided lanes costs four).
+    const int g = (t & 31) >> 1, qg = (t & 1) | ((t >> 5) << 1);
     // Accumulators paired along adjacent outputs: one packed two-lane FMA
     // (fma.rn on each lane, the same rounding as fmaf) per pair.
     constexpr int NP2 = NI >= 2 ? NI / 2 : 1;
@@ -132,7 +144,7 @@ __device__ __forceinline__ void tile_gemm(int t, const float* in, int AS_rt, int
     const bool full = g * NI + NI <= N;  // all NI outputs of this thread exist
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const int row = (qg + 8 * j) * AS;
+        const int row = (qg + 8 * j) * OS;
         float v[NI];
 #pragma unroll
         for (int i = 0; i < NI; ++i) {
@@ -157,16 +169,16 @@ __device__ __forceinline__ void tile_gemm(int t, const float* in, int AS_rt, int
 // One layer for the tile; only the register tiles up to NIMAX outputs per
 // thread are instantiated (NP = 16 NI <= 16 * NIMAX is guaranteed by the
 // launcher). AST as in tile_gemm.
-template <int NIMAX, int AST = 0, bool INPLACE = false>
+template <int NIMAX, int AST = 0, bool INPLACE = false, int OST = 0>
 __device__ __forceinline__ void layer(int t, const float* in, int AS, int K, const float* WT, int NP,
                                       float* out, int N, int mode, const float* mask, int group = 0) {
-    if (NP == 16) tile_gemm<1, AST, INPLACE>(t, in, AS, K, WT, out, N, mode, mask, group);
+    if (NP == 16) tile_gemm<1, AST, INPLACE, OST>(t, in, AS, K, WT, out, N, mode, mask, group);
     else if (NIMAX >= 2 && NP == 32)
-        tile_gemm<(NIMAX >= 2 ? 2 : 1), AST, INPLACE>(t, in, AS, K, WT, out, N, mode, mask, group);
+        tile_gemm<(NIMAX >= 2 ? 2 : 1), AST, INPLACE, OST>(t, in, AS, K, WT, out, N, mode, mask, group);
     else if (NIMAX >= 4 && NP == 64)
-        tile_gemm<(NIMAX >= 4 ? 4 : 1), AST, INPLACE>(t, in, AS, K, WT, out, N, mode, mask, group);
+        tile_gemm<(NIMAX >= 4 ? 4 : 1), AST, INPLACE, OST>(t, in, AS, K, WT, out, N, mode, mask, group);
     else if (NIMAX >= 8)
-        tile_gemm<(NIMAX >= 8 ? 8 : 1), AST, INPLACE>(t, in, AS, K, WT, out, N, mode, mask, group);
+        tile_gemm<(NIMAX >= 8 ? 8 : 1), AST, INPLACE, OST>(t, in, AS, K, WT, out, N, mode, mask, group);
 }
 
 // ------------------------------------------------------------- encode
@@ -543,6 +555,172 @@ __global__ void __launch_bounds__(fwd_max_groups(NIMAX) * kNT, 1) k_forward_fp32
         epilogue_tile<SAMPLE, KH>(t, cfg, act, AS, base, n, S.ld, S.uin, S.ufrac, S.dir, S.pdf, S.mix);
         group_sync(group);
     }
+}
+
+// ------------------------------------- warp-specialised forward kernel
+
+// mbarrier primitives (CTA scope). Waits are bounded: false after ~2^31
+// cycles (about a second), so a broken hand-off ends the kernel with an
+// error status instead of hanging it.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void fbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool fbar_wait(uint32_t bar, uint32_t parity) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        // sleeps in the barrier until the phase completes or ~20 us pass
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.b32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity), "r"(20000u)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > (1ll << 31)) return false;
+    }
+}
+
+// AND of p over the 128 threads of tile group `group` (its named barrier);
+// also orders their memory accesses like group_sync.
+__device__ __forceinline__ bool group_all(int group, bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred q, r;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.and.pred r, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, r;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)p), "r"(group + 1), "r"(kNT)
+        : "memory");
+    return r != 0;
+}
+
+// Row stride (floats) of an encoded tile: the network input width rounded
+// up to 4, plus 4 (the float4 row reads of the first layer stay aligned).
+__host__ __device__ constexpr int enc_stride(int w0) { return (w0 + 3) / 4 * 4 + 4; }
+
+// Producer / consumer form of the fused forward pass. The CTA (one per SM)
+// holds 1 + GC tile groups of 128 threads sharing the weights in shared
+// memory. Group 0 only encodes: it walks the CTA's tiles in order, gathers
+// and blends the grid corners of each (Sec. 5.1, Eq. 11; plus the
+// product-mode encodings) and leaves the encoded tile in the mailbox of the
+// consumer group that owns it. Consumer group g owns the CTA's tiles
+// g, g + GC, g + 2 GC, ...: it runs the MLP (Eq. 12), the first layer
+// straight from its mailbox (released as soon as that layer has read it),
+// and the vMF epilogue (Table 1, Eq. 3-4, Sec. 5.3). The gathers' L2 latency
+// is thus spent by the producer while the consumers keep the FMA pipes busy.
+// Hand-offs use one 'full' and one 'empty' mbarrier per mailbox; one thread
+// per group waits on it (bounded) and the group's named barrier passes the
+// outcome on. A timed-out wait sets kStatusTimeout in *status (if given).
+template <bool SAMPLE, int NIMAX, int KH, int GC, int DEPTH>
+__global__ void __launch_bounds__((GC + 1) * kNT, 1) k_forward_fp32_ws(const __grid_constant__ DevCfg cfg,
+                                                                      const float* __restrict__ grid,
+                                                                      const float* __restrict__ wfwd,
+                                                                      const __grid_constant__ QueryBatch qb,
+                                                                      int* __restrict__ status) {
+    extern __shared__ float4 smem4[];
+    float* sW = reinterpret_cast<float*>(smem4);
+    constexpr int AS = fwd_act_stride(NIMAX);
+    const int ES = enc_stride(cfg.widths[0]);
+    const int group = threadIdx.x / kNT;
+    const int t = threadIdx.x % kNT;
+    constexpr int NB = GC * DEPTH;          // mailboxes: DEPTH per consumer group
+    float* act0 = sW + cfg.fwd_floats;      // GC activation tiles
+    float* box0 = act0 + GC * kTQ * AS;     // NB mailboxes (encoded tiles)
+    uint64_t* bars = reinterpret_cast<uint64_t*>(box0 + NB * kTQ * ES);  // full[NB], empty[NB]
+    for (int i = threadIdx.x; i < cfg.fwd_floats / 4; i += blockDim.x)
+        smem4[i] = __ldg(reinterpret_cast<const float4*>(wfwd) + i);
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2 * NB; ++b) fbar_init(smem_addr(&bars[b]), 1);
+    }
+    __syncthreads();
+    int64_t total = qb.total_tiles, n0 = qb.seg[0].n;
+    if (qb.n_dev) {
+        n0 = *qb.n_dev;
+        total = (n0 + kTQ - 1) / kTQ;
+    }
+    bool ok = true;
+    if (group == 0) {
+        // Producer: tile k of this CTA goes to mailbox k % NB.
+        for (int64_t k = 0; ok; ++k) {
+            const int64_t tile = blockIdx.x + k * gridDim.x;
+            if (tile >= total) break;
+            const int b = (int)(k % NB);
+            const uint32_t use = (uint32_t)(k / NB);
+            // the mailbox's previous tile (if any) has been read
+            bool w = true;
+            if (t == 0) w = fbar_wait(smem_addr(&bars[NB + b]), (use & 1u) ^ 1u);
+            ok = group_all(0, w);
+            if (!ok) break;
+            int sg = 0;
+            while (sg + 1 < qb.nseg && tile >= qb.seg[sg + 1].tile0) ++sg;
+            const QuerySeg& S = qb.seg[sg];
+            const int64_t n = (sg == 0 && qb.n_dev) ? n0 : S.n;
+            const int64_t base = (tile - S.tile0) * kTQ;
+            // four levels' loads in flight where the registers allow (GC <= 3)
+            encode_tile<(GC <= 3)>(t, cfg, grid, base, n, S.ld, S.pos, S.aux, box0 + b * kTQ * ES, ES);
+            // positions of the CTA's next tile into L2
+            if ((t & 31) == 0 && t < 2 * kTQ) {
+                const int64_t nt = tile + gridDim.x;
+                if (nt < total) {
+                    int s2 = sg;
+                    while (s2 + 1 < qb.nseg && nt >= qb.seg[s2 + 1].tile0) ++s2;
+                    const QuerySeg& S2 = qb.seg[s2];
+                    const int64_t b2 = (nt - S2.tile0) * kTQ + (t >> 5) * 16;
+                    for (int r = 0; r < 3; ++r)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(S2.pos + r * S2.ld + b2));
+                }
+            }
+            group_sync(0);
+            if (t == 0) fbar_arrive(smem_addr(&bars[b]));
+        }
+    } else {
+        const int g = group - 1;
+        float* act = act0 + g * kTQ * AS;
+        for (int64_t i = 0; ok; ++i) {
+            const int64_t k = g + i * GC;
+            const int64_t tile = blockIdx.x + k * gridDim.x;
+            if (tile >= total) break;
+            const int b = (int)(k % NB);
+            const float* box = box0 + b * kTQ * ES;
+            bool w = true;
+            if (t == 0) w = fbar_wait(smem_addr(&bars[b]), (uint32_t)((k / NB) & 1));
+            ok = group_all(group, w);
+            if (!ok) break;
+            int sg = 0;
+            while (sg + 1 < qb.nseg && tile >= qb.seg[sg + 1].tile0) ++sg;
+            const QuerySeg& S = qb.seg[sg];
+            const int64_t n = (sg == 0 && qb.n_dev) ? n0 : S.n;
+            const int64_t base = (tile - S.tile0) * kTQ;
+            // this tile's uniforms (or directions) into L2 for the epilogue
+            if ((t & 31) == 0 && t < 3 * 32) {
+                const int64_t jj = base + (t & (kTQ - 1));
+                if (jj < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(S.uin + (t >> 5) * S.ld + jj));
+            }
+            const bool one = cfg.n_layers == 1;
+            layer<NIMAX, 0, false, AS>(t, box, ES, cfg.widths[0], sW + cfg.off_fwd[0], cfg.np_fwd[0], act,
+                                   cfg.widths[1], one ? 0 : 1, nullptr, group);
+            group_sync(group);
+            if (t == 0) fbar_arrive(smem_addr(&bars[NB + b]));  // mailbox read
+            for (int l = 1; l < cfg.n_layers; ++l) {
+                const bool last = l == cfg.n_layers - 1;
+                layer<NIMAX, AS, true>(t, act, AS, cfg.widths[l], sW + cfg.off_fwd[l], cfg.np_fwd[l], act,
+                                       cfg.widths[l + 1], last ? 0 : 1, nullptr, group);
+                group_sync(group);
+            }
+            epilogue_tile<SAMPLE, KH>(t, cfg, act, AS, base, n, S.ld, S.uin, S.ufrac, S.dir, S.pdf, S.mix);
+            group_sync(group);
+        }
+    }
+    if (!ok && t == 0 && status) atomicOr(status, kStatusTimeout);
 }
 
 // ------------------------------------------------------ training kernel
@@ -972,8 +1150,52 @@ static cudaError_t launch_fwd_inst(const DevCfg& cfg, const float* grid, const f
     return cudaGetLastError();
 }
 
+// Mailboxes per consumer group of the warp-specialised kernel.
+constexpr int kWsDepth = 2;
+
+// Shared memory of the warp-specialised kernel with GC consumer groups:
+// weights, GC activation tiles, GC * kWsDepth mailboxes and two mbarriers
+// per mailbox.
+static size_t ws_smem_bytes(const DevCfg& cfg, int I, int GC) {
+    const size_t nb = (size_t)GC * kWsDepth;
+    return sizeof(float) * ((size_t)cfg.fwd_floats + (size_t)GC * kTQ * fwd_act_stride(I) +
+                            nb * kTQ * enc_stride(cfg.widths[0])) +
+           2 * nb * sizeof(uint64_t);
+}
+
+template <bool SAMPLE, int GC>
+static cudaError_t launch_fwd_ws(const DevCfg& cfg, const float* grid, const float* wfwd,
+                                 const QueryBatch& qb, int64_t tiles_hint, int* status, cudaStream_t st) {
+    auto kern = k_forward_fp32_ws<SAMPLE, 4, 4, GC, kWsDepth>;
+    const size_t smem = ws_smem_bytes(cfg, 4, GC);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             carveout_percent(smem + 1024));
+    if (e != cudaSuccess) return e;
+    int64_t g = sm_count();
+    const int64_t need = (tiles_hint + GC - 1) / GC;
+    if (need < g) g = need < 1 ? 1 : need;
+    kern<<<(int)g, (GC + 1) * kNT, smem, st>>>(cfg, grid, wfwd, qb, status);
+    return cudaGetLastError();
+}
+
+// Consumer groups of the warp-specialised kernel for this model, or 0 for
+// the tile-group kernel. It serves the instance with 64-wide register tiles
+// and at most 8 lobes whose buffers fit (the paper-shaped networks).
+// NPM_FP32_WS (0, 3 or 4) overrides the choice for launch sweeps.
+static int ws_groups(const DevCfg& cfg, int inst) {
+    // three consumer groups at 128 registers beat four at 96 (measured)
+    int gc = 3;
+    if (const char* env = getenv("NPM_FP32_WS")) gc = atoi(env);
+    if (gc != 3 && gc != 4) return 0;
+    if (inst != 4 || (cfg.K + 1) / 2 > 4) return 0;
+    if (ws_smem_bytes(cfg, 4, gc) > 227 * 1024) return 0;
+    return gc;
+}
+
 cudaError_t launch_forward_fp32_batch(const DevCfg& cfg, const float* grid, const float* wfwd,
-                                      QueryBatch& qb, int64_t max_n, cudaStream_t st) {
+                                      QueryBatch& qb, int64_t max_n, cudaStream_t st, int* status) {
     int64_t t0 = 0;
     for (int s = 0; s < qb.nseg; ++s) {
         qb.seg[s].tile0 = t0;
@@ -982,6 +1204,13 @@ cudaError_t launch_forward_fp32_batch(const DevCfg& cfg, const float* grid, cons
     qb.total_tiles = t0;
     const int64_t hint = qb.n_dev ? (max_n + kTQ - 1) / kTQ : t0;
     const int inst = fp32_instance(cfg);
+    const int gc = ws_groups(cfg, inst);
+    if (gc == 4)
+        return qb.sample ? launch_fwd_ws<true, 4>(cfg, grid, wfwd, qb, hint, status, st)
+                         : launch_fwd_ws<false, 4>(cfg, grid, wfwd, qb, hint, status, st);
+    if (gc == 3)
+        return qb.sample ? launch_fwd_ws<true, 3>(cfg, grid, wfwd, qb, hint, status, st)
+                         : launch_fwd_ws<false, 3>(cfg, grid, wfwd, qb, hint, status, st);
     if (qb.sample) {
         if (inst == 2) return launch_fwd_inst<true, 2>(cfg, grid, wfwd, qb, hint, st);
         if (inst == 4) return launch_fwd_inst<true, 4>(cfg, grid, wfwd, qb, hint, st);
@@ -995,7 +1224,7 @@ cudaError_t launch_forward_fp32_batch(const DevCfg& cfg, const float* grid, cons
 cudaError_t launch_forward_fp32(const DevCfg& cfg, const float* grid, const float* wfwd, int64_t n,
                                 int64_t ld, const float* pos, const float* aux, const float* uin,
                                 float ufrac, bool sample, float* dir_out, float* pdf_out,
-                                float* mix_out, cudaStream_t st) {
+                                float* mix_out, cudaStream_t st, int* status) {
     QueryBatch qb;
     memset(&qb, 0, sizeof(qb));
     qb.nseg = 1;
@@ -1010,7 +1239,7 @@ cudaError_t launch_forward_fp32(const DevCfg& cfg, const float* grid, const floa
     q.dir = sample ? dir_out : nullptr;
     q.pdf = pdf_out;
     q.mix = sample ? mix_out : nullptr;
-    return launch_forward_fp32_batch(cfg, grid, wfwd, qb, n, st);
+    return launch_forward_fp32_batch(cfg, grid, wfwd, qb, n, st, status);
 }
 
 cudaError_t launch_train_fp32(const DevCfg& cfg, const float* params, int64_t mlp_off,

@@ -46,6 +46,8 @@ struct npm_handle {
 // Parameters and FP32 forward weights that inference evaluates.
 inline const float* inf_params(const npm_handle* h) { return h->ema ? h->ema : h->params; }
 inline const float* inf_wfwd(const npm_handle* h) { return h->ema ? h->wfwd_inf : h->wfwd; }
+// Device status word (kStatus* bits, read by npm_check_device_status).
+inline int* status_word(npm_handle* h) { return reinterpret_cast<int*>(h->scalars + 8); }
 
 namespace npm {
 // Validates cfg and derives the kernels' view of it; ng / nmlp receive the

@@ -17,12 +17,15 @@ size_t train_smem_bytes(const DevCfg& c);
 cudaError_t launch_forward_fp32(const DevCfg& cfg, const float* grid, const float* wfwd, int64_t n,
                                 int64_t ld, const float* pos, const float* aux, const float* uin,
                                 float ufrac, bool sample, float* dir_out, float* pdf_out,
-                                float* mix_out, cudaStream_t st);
+                                float* mix_out, cudaStream_t st, int* status = nullptr);
 
 // Several requests in one launch (segment table; tile offsets filled in
-// here). max_n bounds the device-side count when qb.n_dev is set.
+// here). max_n bounds the device-side count when qb.n_dev is set. status
+// (device word, or NULL) receives kStatusTimeout if a kernel-internal
+// hand-off times out.
 cudaError_t launch_forward_fp32_batch(const DevCfg& cfg, const float* grid, const float* wfwd,
-                                      QueryBatch& qb, int64_t max_n, cudaStream_t st);
+                                      QueryBatch& qb, int64_t max_n, cudaStream_t st,
+                                      int* status = nullptr);
 
 cudaError_t launch_train_fp32(const DevCfg& cfg, const float* params, int64_t mlp_off,
                               const float* wfwd, const float* wbwd, int64_t n, int64_t ld,

@@ -103,16 +103,17 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
-// One potentially blocking test of phase `parity` (the thread may sleep in
-// the barrier for a system-dependent time before it returns false).
+// One potentially blocking test of phase `parity`: the thread sleeps in the
+// barrier until the phase completes or about 20 microseconds pass (the
+// suspend-time hint), so a waiting warp issues almost nothing.
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.b32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(20000u)
         : "memory");
     return ok != 0;
 }
@@ -524,7 +525,7 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? 6 : (KMAX == 8 
                 *reinterpret_cast<uint4*>(sA0 + a0_lo + tile_off(t, 8 * c, kp0)) = make_uint4(0u, 0u, 0u, 0u);
         }
     }
-    bool ok = !__syncthreads_or(!mbar_wait_bounded(bar_w, 0));
+    bool ok = !__syncthreads_or(warp == 0 && !mbar_wait_bounded(bar_w, 0));
     uint32_t phase = 0;
     const uint32_t sA_addr = smem_u32(sA), sA0_addr = smem_u32(sA0);
     const uint32_t sW_addr = smem_u32(sW);
@@ -574,7 +575,10 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? 6 : (KMAX == 8 
                 }
                 mma_commit(bar_mma);
             }
-            const bool done = mbar_wait_bounded(bar_mma, phase);
+            // Warp 0 (which holds the issuing thread) waits on the MMA's
+            // barrier; the other warps wait in the CTA barrier, issuing
+            // nothing, and see the accumulators after its fence.
+            const bool done = warp != 0 || mbar_wait_bounded(bar_mma, phase);
             phase ^= 1u;
             ok = !__syncthreads_or(!done);
             if (!ok) break;
