@@ -125,9 +125,9 @@ def mlp_flops(w):
     return 2 * sum(a * b for a, b in zip(w.widths[:-1], w.widths[1:]))
 
 
-# DRAM bytes of one k_forward_fp32 launch on the paper-shaped workload
+# DRAM bytes of one k_forward_fp32_ws launch on the paper-shaped workload
 # (2^20 queries) from the ncu capture summarised in profiles/.
-FP32_FORWARD_DRAM_BYTES = 66717952 + 9522688
+FP32_FORWARD_DRAM_BYTES = 66750720 + 8851968
 
 # Algorithmic work per query of the tensor-core forward on the tiny model
 # (K = 4): transcendentals of the vMF decode, sample and pdf (softmax 4,
@@ -535,11 +535,13 @@ def main():
         "roofline": ({"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                       "frac": achieved / alu_peak, "traffic": FP32_FORWARD_DRAM_BYTES,
                       "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one 2^20-query "
-                                      "launch (profiles/k_forward_fp32_paper_hash_2e20.md); ncu flushes "
+                                      "launch (profiles/k_forward_fp32_ws_paper_hash_2e20.md); ncu flushes "
                                       "the caches before the capture, so it includes the 41.7 MB FP32 "
                                       "grid table that stays in L2 between calls; algorithmic HBM "
-                                      "bytes are 40 per query (41.9 MB)",
-                      "kernel": "k_forward_fp32<sample>",
+                                      "bytes are 40 per query (41.9 MB). The same capture "
+                                      "shows the L1TEX data pipe at 82 % of its peak wavefront "
+                                      "rate (grid gathers plus the MLP's shared-memory operands)",
+                      "kernel": "k_forward_fp32_ws<sample>",
                       "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"}
                      if (w.precision == synth.FP32 and not train_mode) else None),
         "clocks": clocks,
