@@ -303,14 +303,16 @@ __device__ __forceinline__ float vmf_eval_fast(const Lobe& L, float cn, float wx
 // close to the mean.
 __device__ __forceinline__ float vmf_sample_t(float k, float u1) {
     if (!(k > 1e-20f)) return 2.0f * u1;
-    float t = -log1pf(u1 * expm1f(-2.0f * k)) / k;
+    // the quotient is at most 2 and k far below 2^126: the fast divide is
+    // within 2 ulp
+    float t = __fdividef(-log1pf(u1 * expm1f(-2.0f * k)), k);
     return fminf(fmaxf(t, 0.0f), 2.0f);
 }
 
 // Orthonormal basis (t, b) completing unit vector n (Duff et al. 2017).
 __device__ __forceinline__ void frame(const float n[3], float t[3], float b[3]) {
     float sg = n[2] >= 0.0f ? 1.0f : -1.0f;
-    float a = -1.0f / (sg + n[2]);
+    float a = -__fdividef(1.0f, sg + n[2]);  // |sg + n_z| in [1, 2]
     float bb = n[0] * n[1] * a;
     t[0] = 1.0f + sg * n[0] * n[0] * a;
     t[1] = sg * bb;

@@ -364,7 +364,7 @@ __device__ __forceinline__ void decode_half(const DevCfg& cfg, const float* raw,
             ssum += hm.lob[ii].lam;
         }
     ssum += __shfl_xor_sync(kFull, ssum, 1);
-    const float inv = 1.0f / ssum;
+    const float inv = __fdividef(1.0f, ssum);  // ssum in [1, K]
 #pragma unroll
     for (int ii = 0; ii < KH; ++ii)
         if (ii < hm.cnt) {

@@ -181,6 +181,36 @@ __device__ __forceinline__ void store16(uint8_t* sA, uint32_t off0, uint32_t off
     }
 }
 
+// Forward-pass form of store16. With a residual tile, hi is v truncated to
+// BF16 (its upper 16 bits: one byte permute per pair) and the residual
+// v - hi, exact in FP32 and of the same sign as v, is rounded to BF16 (one
+// packed subtraction and one conversion per pair); the product error that
+// split BF16 drops stays below 2^-15 relative. Without a residual tile, v is
+// rounded to nearest.
+__device__ __forceinline__ void store16_fwd(uint8_t* sA, uint32_t off0, uint32_t off1, const float (&v)[16],
+                                            uint32_t lo_off) {
+    uint32_t h[8];
+    if (lo_off) {
+        uint32_t l[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t a = __float_as_uint(v[2 * i]), b = __float_as_uint(v[2 * i + 1]);
+            h[i] = __byte_perm(a, b, 0x7632);
+            const float2 nh = make_float2(__uint_as_float((a & 0xffff0000u) ^ 0x80000000u),
+                                          __uint_as_float((b & 0xffff0000u) ^ 0x80000000u));
+            const float2 r = __fadd2_rn(make_float2(v[2 * i], v[2 * i + 1]), nh);
+            l[i] = pack_bf16(r.x, r.y);
+        }
+        *reinterpret_cast<uint4*>(sA + lo_off + off0) = make_uint4(l[0], l[1], l[2], l[3]);
+        *reinterpret_cast<uint4*>(sA + lo_off + off1) = make_uint4(l[4], l[5], l[6], l[7]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) h[i] = pack_bf16(v[2 * i], v[2 * i + 1]);
+    }
+    *reinterpret_cast<uint4*>(sA + off0) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(sA + off1) = make_uint4(h[4], h[5], h[6], h[7]);
+}
+
 // One or two BF16 values (and their residuals when lo_off != 0).
 __device__ __forceinline__ void store_pair(uint8_t* sA, uint32_t off, float a, float b, uint32_t lo_off) {
     __nv_bfloat162 hb = __floats2bfloat162_rn(a, b);
@@ -262,6 +292,50 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
     }
     const int F = F2 ? 2 : cfg.feat;
     int l = lbeg;
+    if (!F2 && (F == 4 || F == 8) && lbeg == 0 && lend == 1 && tail && !pad_all &&
+        cfg.mode != NPM_PRODUCT) {
+        // A single level of 4 or 8 features fills the first 8-column chunk
+        // (features, then zeros): one 16-byte store (and one for residuals).
+        const Cell cl = make_cell(x, y, z, cfg.level_res[0]);
+        uint32_t idx[8];
+        corner_idx8(cfg, 0, cl, idx);
+        float ws[8];
+        corner_w8(cl, ws);
+        float e[8];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (h == 0 || F == 8) {
+                decltype(load_raw4(grid_h, 0u, F, 0)) raw[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) raw[c] = load_raw4(grid_h, idx[c], F, h);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float4 v = widen4(raw[c]);
+                    acc.x = fmaf(ws[c], v.x, acc.x);
+                    acc.y = fmaf(ws[c], v.y, acc.y);
+                    acc.z = fmaf(ws[c], v.z, acc.z);
+                    acc.w = fmaf(ws[c], v.w, acc.w);
+                }
+            }
+            e[4 * h] = acc.x;
+            e[4 * h + 1] = acc.y;
+            e[4 * h + 2] = acc.z;
+            e[4 * h + 3] = acc.w;
+        }
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __nv_bfloat162 hb = __floats2bfloat162_rn(e[2 * i], e[2 * i + 1]);
+            hw[i] = *reinterpret_cast<uint32_t*>(&hb);
+            const float2 hf = __bfloat1622float2(hb);
+            lw[i] = pack_bf16(e[2 * i] - hf.x, e[2 * i + 1] - hf.y);
+        }
+        const uint32_t off = tile_off(row, 0, kp);
+        *reinterpret_cast<uint4*>(sA + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        if (lo) *reinterpret_cast<uint4*>(sA + lo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        return;
+    }
     if constexpr (F2) {
         for (; l + 1 < lend; l += 2) {
             const Cell c0 = make_cell(x, y, z, cfg.level_res[l]);
@@ -395,7 +469,7 @@ __device__ __forceinline__ void tc_decode(const TcCfg& tc, const float (&raw)[4 
             lob[i].lam = __expf(raw[4 * i] - mx);
             ssum += lob[i].lam;
         }
-    const float inv = 1.0f / ssum;
+    const float inv = __fdividef(1.0f, ssum);  // ssum in [1, K]
 #pragma unroll
     for (int i = 0; i < KMAX; ++i)
         if (i < K) {
@@ -593,8 +667,8 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? 6 : (KMAX == 8 
                     float v[16];
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] = fmaxf(__uint_as_float(r[i]), 0.0f);
-                    store16(sA, tile_off(t, c0, kp_next), tile_off(t, c0 + 8, kp_next), v,
-                            tc.split ? tc.a_bytes : 0u);
+                    store16_fwd(sA, tile_off(t, c0, kp_next), tile_off(t, c0 + 8, kp_next), v,
+                                tc.split ? tc.a_bytes : 0u);
                 }
                 fence_async_smem();
                 tc_fence_before();
