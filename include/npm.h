@@ -420,6 +420,22 @@ npm_status npm_load(npm_handle* h, const char* path);
  * wait timeouts). Synchronises the stream. */
 npm_status npm_check_device_status(npm_handle* h, void* stream);
 
+/* Bound of the device-side waits inside the FP32 forward kernel of this
+ * handle (its encoder and MLP thread groups hand tiles over through
+ * shared-memory mailboxes; failure handling, not part of the method).
+ *   cycles > 0: a wait gives up after about `cycles` SM clock cycles
+ *               (default 2^31, about a second at 2 GHz);
+ *   cycles <= 0: every wait is one non-blocking test, so a hand-off that is
+ *               not already complete gives up at once (this lets a test
+ *               exercise the timeout path without waiting).
+ * A wait that gives up ends the kernel early: the outputs of that call are
+ * incomplete and npm_check_device_status then returns NPM_ERR_TIMEOUT. The
+ * kernel issues no asynchronous copies, so nothing is left in flight and the
+ * context stays usable. Applies to launches made after the call; the
+ * tensor-core kernels keep their fixed bound. Errors: NPM_ERR_INVALID_ARG
+ * (NULL handle). */
+npm_status npm_set_wait_limit(npm_handle* h, int64_t cycles);
+
 /* Thread-local text of the last error returned on this thread. */
 const char* npm_last_error(void);
 

@@ -242,6 +242,11 @@ class NPM:
         _lib.check(self._L.npm_check_device_status(self._h, _stream_ptr(stream)),
                    "npm_check_device_status")
 
+    def set_wait_limit(self, cycles: int):
+        """Bound (SM clock cycles) of the FP32 forward kernel's internal
+        waits (npm_set_wait_limit); <= 0 makes each wait one test."""
+        _lib.check(self._L.npm_set_wait_limit(self._h, int(cycles)), "npm_set_wait_limit")
+
 
 class Server:
     """Continuous-batching request loop over one NPM model (npm_server_* C

@@ -414,7 +414,7 @@ npm_status npm_query_sample(npm_handle* h, int64_t n, const float* pos, const fl
     cudaStream_t st = (cudaStream_t)stream;
     if (h->tc) return npm::tc_query(h, n, ld, pos, aux, u, uniform_frac, true, dir_out, pdf_out, mix_out, st);
     NPM_CUDA(npm::launch_forward_fp32(h->dc, inf_params(h), inf_wfwd(h), n, ld, pos, aux, u, uniform_frac,
-                                      true, dir_out, pdf_out, mix_out, st, status_word(h)),
+                                      true, dir_out, pdf_out, mix_out, st, status_word(h), h->wait_limit),
              "query_sample launch");
     return NPM_OK;
 }
@@ -483,7 +483,7 @@ npm_status npm_eval_pdf(npm_handle* h, int64_t n, const float* pos, const float*
     cudaStream_t st = (cudaStream_t)stream;
     if (h->tc) return npm::tc_query(h, n, ld, pos, aux, dir, 0.0f, false, nullptr, pdf_out, nullptr, st);
     NPM_CUDA(npm::launch_forward_fp32(h->dc, inf_params(h), inf_wfwd(h), n, ld, pos, aux, dir, 0.0f, false,
-                                      nullptr, pdf_out, nullptr, st, status_word(h)),
+                                      nullptr, pdf_out, nullptr, st, status_word(h), h->wait_limit),
              "eval_pdf launch");
     return NPM_OK;
 }
@@ -577,6 +577,12 @@ npm_status npm_check_device_status(npm_handle* h, void* stream) {
     NPM_CUDA(cudaStreamSynchronize(st), "synchronise");
     if (word & npm::kStatusTimeout) return fail(NPM_ERR_TIMEOUT, "a device-side wait timed out");
     if (word & npm::kStatusNumeric) return fail(NPM_ERR_NUMERIC, "non-finite loss; Adam step skipped");
+    return NPM_OK;
+}
+
+npm_status npm_set_wait_limit(npm_handle* h, int64_t cycles) {
+    if (!h) return fail(NPM_ERR_INVALID_ARG, "handle is NULL");
+    h->wait_limit = cycles;
     return NPM_OK;
 }
 

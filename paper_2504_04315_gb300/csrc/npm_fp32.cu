@@ -559,9 +559,10 @@ __global__ void __launch_bounds__(fwd_max_groups(NIMAX) * kNT, 1) k_forward_fp32
 
 // ------------------------------------- warp-specialised forward kernel
 
-// mbarrier primitives (CTA scope). Waits are bounded: false after ~2^31
-// cycles (about a second), so a broken hand-off ends the kernel with an
-// error status instead of hanging it.
+// mbarrier primitives (CTA scope). Waits are bounded: false after `limit`
+// SM clock cycles (2^31 by default, about a second), so a broken hand-off
+// ends the kernel with an error status instead of hanging it. limit <= 0
+// makes the wait one non-blocking test.
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -571,7 +572,18 @@ __device__ __forceinline__ void fbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void fbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ bool fbar_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool fbar_wait(uint32_t bar, uint32_t parity, long long limit) {
+    if (limit <= 0) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.test_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        return ok != 0;
+    }
     const long long t0 = clock64();
     for (;;) {
         uint32_t ok;
@@ -584,7 +596,7 @@ __device__ __forceinline__ bool fbar_wait(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity), "r"(20000u)
             : "memory");
         if (ok) return true;
-        if (clock64() - t0 > (1ll << 31)) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
@@ -619,13 +631,16 @@ __host__ __device__ constexpr int enc_stride(int w0) { return (w0 + 3) / 4 * 4 +
 // is thus spent by the producer while the consumers keep the FMA pipes busy.
 // Hand-offs use one 'full' and one 'empty' mbarrier per mailbox; one thread
 // per group waits on it (bounded) and the group's named barrier passes the
-// outcome on. A timed-out wait sets kStatusTimeout in *status (if given).
+// outcome on. A wait that gives up after wait_limit cycles sets
+// kStatusTimeout in *status (if given) and every group leaves its loop; the
+// kernel issues no asynchronous copies, so nothing is left in flight.
 template <bool SAMPLE, int NIMAX, int KH, int GC, int DEPTH>
 __global__ void __launch_bounds__((GC + 1) * kNT, 1) k_forward_fp32_ws(const __grid_constant__ DevCfg cfg,
                                                                       const float* __restrict__ grid,
                                                                       const float* __restrict__ wfwd,
                                                                       const __grid_constant__ QueryBatch qb,
-                                                                      int* __restrict__ status) {
+                                                                      int* __restrict__ status,
+                                                                      long long wait_limit) {
     extern __shared__ float4 smem4[];
     float* sW = reinterpret_cast<float*>(smem4);
     constexpr int AS = fwd_act_stride(NIMAX);
@@ -657,7 +672,7 @@ __global__ void __launch_bounds__((GC + 1) * kNT, 1) k_forward_fp32_ws(const __g
             const uint32_t use = (uint32_t)(k / NB);
             // the mailbox's previous tile (if any) has been read
             bool w = true;
-            if (t == 0) w = fbar_wait(smem_addr(&bars[NB + b]), (use & 1u) ^ 1u);
+            if (t == 0) w = fbar_wait(smem_addr(&bars[NB + b]), (use & 1u) ^ 1u, wait_limit);
             ok = group_all(0, w);
             if (!ok) break;
             int sg = 0;
@@ -692,7 +707,7 @@ __global__ void __launch_bounds__((GC + 1) * kNT, 1) k_forward_fp32_ws(const __g
             const int b = (int)(k % NB);
             const float* box = box0 + b * kTQ * ES;
             bool w = true;
-            if (t == 0) w = fbar_wait(smem_addr(&bars[b]), (uint32_t)((k / NB) & 1));
+            if (t == 0) w = fbar_wait(smem_addr(&bars[b]), (uint32_t)((k / NB) & 1), wait_limit);
             ok = group_all(group, w);
             if (!ok) break;
             int sg = 0;
@@ -1165,7 +1180,8 @@ static size_t ws_smem_bytes(const DevCfg& cfg, int I, int GC) {
 
 template <bool SAMPLE, int GC>
 static cudaError_t launch_fwd_ws(const DevCfg& cfg, const float* grid, const float* wfwd,
-                                 const QueryBatch& qb, int64_t tiles_hint, int* status, cudaStream_t st) {
+                                 const QueryBatch& qb, int64_t tiles_hint, int* status, long long wait_limit,
+                                 cudaStream_t st) {
     auto kern = k_forward_fp32_ws<SAMPLE, 4, 4, GC, kWsDepth>;
     const size_t smem = ws_smem_bytes(cfg, 4, GC);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1176,7 +1192,7 @@ static cudaError_t launch_fwd_ws(const DevCfg& cfg, const float* grid, const flo
     int64_t g = sm_count();
     const int64_t need = (tiles_hint + GC - 1) / GC;
     if (need < g) g = need < 1 ? 1 : need;
-    kern<<<(int)g, (GC + 1) * kNT, smem, st>>>(cfg, grid, wfwd, qb, status);
+    kern<<<(int)g, (GC + 1) * kNT, smem, st>>>(cfg, grid, wfwd, qb, status, wait_limit);
     return cudaGetLastError();
 }
 
@@ -1195,7 +1211,8 @@ static int ws_groups(const DevCfg& cfg, int inst) {
 }
 
 cudaError_t launch_forward_fp32_batch(const DevCfg& cfg, const float* grid, const float* wfwd,
-                                      QueryBatch& qb, int64_t max_n, cudaStream_t st, int* status) {
+                                      QueryBatch& qb, int64_t max_n, cudaStream_t st, int* status,
+                                      long long wait_limit) {
     int64_t t0 = 0;
     for (int s = 0; s < qb.nseg; ++s) {
         qb.seg[s].tile0 = t0;
@@ -1206,11 +1223,11 @@ cudaError_t launch_forward_fp32_batch(const DevCfg& cfg, const float* grid, cons
     const int inst = fp32_instance(cfg);
     const int gc = ws_groups(cfg, inst);
     if (gc == 4)
-        return qb.sample ? launch_fwd_ws<true, 4>(cfg, grid, wfwd, qb, hint, status, st)
-                         : launch_fwd_ws<false, 4>(cfg, grid, wfwd, qb, hint, status, st);
+        return qb.sample ? launch_fwd_ws<true, 4>(cfg, grid, wfwd, qb, hint, status, wait_limit, st)
+                         : launch_fwd_ws<false, 4>(cfg, grid, wfwd, qb, hint, status, wait_limit, st);
     if (gc == 3)
-        return qb.sample ? launch_fwd_ws<true, 3>(cfg, grid, wfwd, qb, hint, status, st)
-                         : launch_fwd_ws<false, 3>(cfg, grid, wfwd, qb, hint, status, st);
+        return qb.sample ? launch_fwd_ws<true, 3>(cfg, grid, wfwd, qb, hint, status, wait_limit, st)
+                         : launch_fwd_ws<false, 3>(cfg, grid, wfwd, qb, hint, status, wait_limit, st);
     if (qb.sample) {
         if (inst == 2) return launch_fwd_inst<true, 2>(cfg, grid, wfwd, qb, hint, st);
         if (inst == 4) return launch_fwd_inst<true, 4>(cfg, grid, wfwd, qb, hint, st);
@@ -1224,7 +1241,7 @@ cudaError_t launch_forward_fp32_batch(const DevCfg& cfg, const float* grid, cons
 cudaError_t launch_forward_fp32(const DevCfg& cfg, const float* grid, const float* wfwd, int64_t n,
                                 int64_t ld, const float* pos, const float* aux, const float* uin,
                                 float ufrac, bool sample, float* dir_out, float* pdf_out,
-                                float* mix_out, cudaStream_t st, int* status) {
+                                float* mix_out, cudaStream_t st, int* status, long long wait_limit) {
     QueryBatch qb;
     memset(&qb, 0, sizeof(qb));
     qb.nseg = 1;
@@ -1239,7 +1256,7 @@ cudaError_t launch_forward_fp32(const DevCfg& cfg, const float* grid, const floa
     q.dir = sample ? dir_out : nullptr;
     q.pdf = pdf_out;
     q.mix = sample ? mix_out : nullptr;
-    return launch_forward_fp32_batch(cfg, grid, wfwd, qb, n, st, status);
+    return launch_forward_fp32_batch(cfg, grid, wfwd, qb, n, st, status, wait_limit);
 }
 
 cudaError_t launch_train_fp32(const DevCfg& cfg, const float* params, int64_t mlp_off,

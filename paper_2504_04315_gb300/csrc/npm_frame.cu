@@ -225,7 +225,7 @@ npm_status enqueue_frame(npm_wavefront* w, cudaStream_t st) {
         q.pdf = s.pdf;
         q.ufrac = w->cfg.uniform_frac;
         cudaError_t e = h->tc ? npm::tc_query_batch(h, qb, s.P, st)
-                              : npm::launch_forward_fp32_batch(h->dc, inf_params(h), inf_wfwd(h), qb, s.P, st, status_word(h));
+                              : npm::launch_forward_fp32_batch(h->dc, inf_params(h), inf_wfwd(h), qb, s.P, st, status_word(h), h->wait_limit);
         if (e != cudaSuccess) return npm::set_error(NPM_ERR_CUDA, cudaGetErrorString(e));
         k_wf_advance<<<g, 256, 0, st>>>(s, b, src);
         k_wf_stamp<<<1, 32, 0, st>>>(s, 1 + b);

@@ -41,6 +41,8 @@ struct npm_handle {
     float* ema = nullptr;
     float* wfwd_inf = nullptr;
     float ema_decay = 0.0f;
+    // Bound of the FP32 forward kernel's internal waits (npm_set_wait_limit).
+    long long wait_limit = 1ll << 31;
 };
 
 // Parameters and FP32 forward weights that inference evaluates.

@@ -9,6 +9,10 @@
 
 namespace npm {
 
+// Default bound of a kernel-internal wait: 2^31 SM clock cycles (about a
+// second at 2 GHz).
+constexpr long long kDefaultWaitLimit = 1ll << 31;
+
 size_t fwd_smem_bytes(const DevCfg& c);
 // Shared-memory carveout (percent of the maximum) that holds `bytes`.
 int carveout_percent(size_t bytes);
@@ -17,15 +21,17 @@ size_t train_smem_bytes(const DevCfg& c);
 cudaError_t launch_forward_fp32(const DevCfg& cfg, const float* grid, const float* wfwd, int64_t n,
                                 int64_t ld, const float* pos, const float* aux, const float* uin,
                                 float ufrac, bool sample, float* dir_out, float* pdf_out,
-                                float* mix_out, cudaStream_t st, int* status = nullptr);
+                                float* mix_out, cudaStream_t st, int* status = nullptr,
+                                long long wait_limit = kDefaultWaitLimit);
 
 // Several requests in one launch (segment table; tile offsets filled in
 // here). max_n bounds the device-side count when qb.n_dev is set. status
 // (device word, or NULL) receives kStatusTimeout if a kernel-internal
-// hand-off times out.
+// hand-off gives up after wait_limit SM clock cycles (<= 0: one
+// non-blocking test per wait).
 cudaError_t launch_forward_fp32_batch(const DevCfg& cfg, const float* grid, const float* wfwd,
                                       QueryBatch& qb, int64_t max_n, cudaStream_t st,
-                                      int* status = nullptr);
+                                      int* status = nullptr, long long wait_limit = kDefaultWaitLimit);
 
 cudaError_t launch_train_fp32(const DevCfg& cfg, const float* params, int64_t mlp_off,
                               const float* wfwd, const float* wbwd, int64_t n, int64_t ld,

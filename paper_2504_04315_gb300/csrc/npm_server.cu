@@ -220,7 +220,7 @@ void launch_batch(npm_server* s, Batch* b) {
             max_n = std::max(max_n, r->n);
         }
         cudaError_t e = h->tc ? npm::tc_query_batch(h, qb, max_n, st)
-                              : npm::launch_forward_fp32_batch(h->dc, inf_params(h), inf_wfwd(h), qb, max_n, st, status_word(h));
+                              : npm::launch_forward_fp32_batch(h->dc, inf_params(h), inf_wfwd(h), qb, max_n, st, status_word(h), h->wait_limit);
         for (Request* r : b->reqs) {
             r->status = e == cudaSuccess ? NPM_OK : NPM_ERR_CUDA;
             copy_rows(r->dir_out, r->ld, row(s, R_DIR, r->off), s->P, 3, r->n, cudaMemcpyDeviceToHost, st);

@@ -246,3 +246,31 @@ def test_checkpoint_round_trip(tmp_path):
     m2.train_step(cuda(b.pos), cuda(b.dir), cuda(b.radiance), cuda(b.pdf))
     # Identical up to the summation order of the gradient atomics.
     assert (np.abs(m.get_params() - m2.get_params()) < 1e-6).mean() > 0.999
+
+
+def test_bounded_wait_timeout_is_reported_and_context_survives():
+    # The paper-shaped FP32 forward hands each tile from its encoder thread
+    # group to an MLP group through shared-memory mailboxes guarded by
+    # mbarriers whose waits are bounded. With a zero wait budget every wait
+    # is one non-blocking test, and the MLP groups' first wait (before the
+    # encoder has finished a tile) gives up: the kernel ends early and
+    # reports NPM_ERR_TIMEOUT; nothing hangs. With the default budget the
+    # next call on the same handle and context is correct again.
+    from paper_2504_04315_gb300 import _lib
+    w = synth.PAPER_HASH
+    n = 1 << 16
+    params = synth.random_params(w, 3)
+    pos = synth.positions(11, n)
+    u = synth.sample_uniforms(11, n)
+    m = make_model(w, params, n)
+    m.set_wait_limit(0)
+    m.query_sample(cuda(pos), cuda(u))
+    with pytest.raises(_lib.NpmError) as exc:
+        m.check_device_status()
+    assert exc.value.status == _lib.ERR_TIMEOUT
+    m.set_wait_limit(1 << 31)
+    d, p, _ = m.query_sample(cuda(pos), cuda(u))
+    m.check_device_status()
+    pick = np.arange(0, n, 16)
+    compare_samples(w, params, pos[:, pick], u[:, pick], None, 0.0, host(d)[:, pick], host(p)[pick],
+                    PDF_RTOL_FP32, DIR_TOL_FP32, MARGIN_FP32)
