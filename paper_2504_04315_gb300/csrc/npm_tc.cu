@@ -886,13 +886,65 @@ __device__ __forceinline__ void scatter_levels(const DevCfg& cfg, float* __restr
     }
 }
 
+// Grid features of a training batch for 2-feature grids (Sec. 5.1, Eq. 11):
+// enc[j][2l + f] = sum_corners w_c V_l[corner][f] from the FP32 master
+// table, in the FP32 arithmetic of tc_encode (same corners, weights and FMA
+// order). One thread per (sample, group of LPT levels), all of a group's
+// corner loads in flight; a full-occupancy kernel without shared memory
+// keeps the whole L1 and many warps for these random L2 reads, which the
+// training kernel (one CTA per SM holding most of the shared memory) cannot.
+template <int LPT>
+__global__ void __launch_bounds__(256) k_train_encode(const __grid_constant__ DevCfg cfg,
+                                                      const float* __restrict__ grid32, int64_t n,
+                                                      int64_t ld, const float* __restrict__ pos,
+                                                      float* __restrict__ enc) {
+    const int ng = (cfg.n_levels + LPT - 1) / LPT;
+    const int G = cfg.grid_feats;
+    const int64_t total = n * ng;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = i / ng;
+        const int l0 = (int)(i - j * ng) * LPT;
+        const float x = pos[j], y = pos[ld + j], z = pos[2 * ld + j];
+        Cell cs[LPT];
+        float2 v[LPT][8];
+#pragma unroll
+        for (int r = 0; r < LPT; ++r) {
+            const int l = l0 + r;
+            if (l < cfg.n_levels) {
+                cs[r] = make_cell(x, y, z, cfg.level_res[l]);
+                const float* gr = grid32 + (size_t)cfg.level_off[l] * 2;
+#pragma unroll
+                for (int c = 0; c < 8; c += 2)
+                    gather_pair2(gr, cfg.level_off[l], corner_idx1(cfg, l, cs[r], c), corner_idx1(cfg, l, cs[r], c + 1),
+                                 v[r][c], v[r][c + 1]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < LPT; ++r) {
+            const int l = l0 + r;
+            if (l < cfg.n_levels) {
+                float ws[8];
+                corner_w8(cs[r], ws);
+                float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    a0 = fmaf(ws[c], v[r][c].x, a0);
+                    a1 = fmaf(ws[c], v[r][c].y, a1);
+                }
+                *reinterpret_cast<float2*>(enc + j * G + 2 * l) = make_float2(a0, a1);
+            }
+        }
+    }
+}
+
 template <int KMAX, bool F2>
 __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(
     const __grid_constant__ TcCfg tc, const __grid_constant__ TcTrain tt, const float* __restrict__ grid32,
     const uint8_t* __restrict__ wblob, int64_t n, int64_t ld, const float* __restrict__ pos,
     const float* __restrict__ aux, const float* __restrict__ dir, const float* __restrict__ rad,
     const float* __restrict__ spdf, const float* __restrict__ dlogv, float inv_n, float* __restrict__ grad,
-    int64_t mlp_off, float* __restrict__ loss, int* __restrict__ status) {
+    int64_t mlp_off, float* __restrict__ loss, int* __restrict__ status, const float* __restrict__ enc) {
     extern __shared__ __align__(1024) uint8_t smem[];
     constexpr int KH = KMAX / 2;
     uint8_t* sW = smem;
@@ -945,8 +997,22 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(
     for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
         const int64_t j = tile * kTile + row;
         const bool valid = j < n;
-        tc_encode<F2>(tc, grid32, j, valid, ld, pos, aux, smem + tt.h_off[0], row, tc.split ? tc.a_bytes : 0u,
-                      true, lv0, lv1, half == 1);
+        if (F2 && enc) {
+            // This half's grid features from k_train_encode (two per level),
+            // then the product-mode inputs and the padding.
+            const int kp0 = tc.layer[0].Kp;
+            const uint32_t lo = tc.split ? tc.a_bytes : 0u;
+            const float* er = enc + (valid ? j : 0) * (int64_t)cfg.grid_feats;
+            for (int l = lv0; l < lv1; ++l) {
+                const float2 v = valid ? __ldg(reinterpret_cast<const float2*>(er + 2 * l)) : make_float2(0.0f, 0.0f);
+                store_pair(smem + tt.h_off[0], tile_off(row, 2 * l, kp0), v.x, v.y, lo);
+            }
+            tc_encode<F2>(tc, grid32, j, valid, ld, pos, aux, smem + tt.h_off[0], row, lo, true, lv1, lv1,
+                          half == 1);
+        } else {
+            tc_encode<F2>(tc, grid32, j, valid, ld, pos, aux, smem + tt.h_off[0], row, tc.split ? tc.a_bytes : 0u,
+                          true, lv0, lv1, half == 1);
+        }
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -1159,6 +1225,10 @@ struct TcState {
     TcCfg train_cfg;     // single-pass BF16 copy of cfg for training
     TcTrain train;
     bool can_train = false;
+    // Grid features of a training batch (max_batch x grid_feats FP32) for
+    // 2-feature grids, written by k_train_encode; NULL: the training kernel
+    // gathers them itself.
+    float* enc = nullptr;
 };
 
 static int pad16(int v) { return (v + 15) / 16 * 16; }
@@ -1263,6 +1333,13 @@ npm_status tc_create(npm_handle* h) {
         return NPM_ERR_OOM;
     }
     cudaMemset(s->wblob, 0, nsplit * t.w_bytes);
+    if (s->can_train && c.feat_per_level == 2) {
+        // Optional: without it the training kernel encodes in place.
+        if (cudaMalloc(&s->enc, sizeof(float) * (size_t)c.max_batch * h->dc.grid_feats) != cudaSuccess) {
+            cudaGetLastError();
+            s->enc = nullptr;
+        }
+    }
     h->tc = s;
     return NPM_OK;
 }
@@ -1271,6 +1348,7 @@ void tc_destroy(npm_handle* h) {
     if (!h->tc) return;
     if (h->tc->wblob) cudaFree(h->tc->wblob);
     if (h->tc->wblob_inf) cudaFree(h->tc->wblob_inf);
+    if (h->tc->enc) cudaFree(h->tc->enc);
     delete h->tc;
     h->tc = nullptr;
 }
@@ -1349,9 +1427,24 @@ static cudaError_t launch_train_tc(npm_handle* h, int64_t n, int64_t ld, const f
     const int64_t ntiles = (n + kTile - 1) / kTile;
     const int g = (int)(ntiles < sms ? ntiles : sms);
     int* status = reinterpret_cast<int*>(h->scalars + 8);
+    const float* enc = nullptr;
+    if (F2 && s->enc && n <= h->cfg.max_batch) {
+        // Levels per thread: two (64 registers, more warps) measured a little
+        // faster than four; tuning override NPM_ENC_LPT (2 or 4).
+        int lpt = 2;
+        if (const char* env = getenv("NPM_ENC_LPT")) lpt = atoi(env) == 4 ? 4 : 2;
+        const int64_t items = n * ((h->dc.n_levels + lpt - 1) / lpt);
+        int64_t eg = (items + 255) / 256;
+        if (eg > (int64_t)sms * 16) eg = (int64_t)sms * 16;
+        if (lpt == 2) k_train_encode<2><<<(int)eg, 256, 0, st>>>(h->dc, h->params, n, ld, pos, s->enc);
+        else k_train_encode<4><<<(int)eg, 256, 0, st>>>(h->dc, h->params, n, ld, pos, s->enc);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        enc = s->enc;
+    }
     kern<<<g < 1 ? 1 : g, kTrainThreads, s->train.smem, st>>>(s->train_cfg, s->train, h->params, s->wblob, n, ld, pos,
                                                          aux, dir, rad, spdf, dlogv, 1.0f / (float)n, h->grads,
-                                                         h->mlp_off, loss, status);
+                                                         h->mlp_off, loss, status, enc);
     return cudaGetLastError();
 }
 
