@@ -530,8 +530,10 @@ def main():
         "e2e": e2e,
         # Kernels per step: one fused query kernel; a training step launches
         # the training kernel, Adam, the step counter, the FP32 weight
-        # arrangement, the loss copy, and on tensor cores the BF16 weights.
-        "gpu_launches": K * ((6 if w.precision != synth.FP32 else 5) if train_mode else 1),
+        # arrangement and the loss copy, and on tensor cores also the BF16
+        # weights, the FP16 grid copy and (2-feature grids) the encode kernel.
+        "gpu_launches": K * ((7 + (1 if w.feat == 2 else 0) if w.precision != synth.FP32 else 5)
+                             if train_mode else 1),
         "roofline": ({"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                       "frac": achieved / alu_peak, "traffic": FP32_FORWARD_DRAM_BYTES,
                       "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one 2^20-query "
