@@ -993,6 +993,33 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(
     const int lv0 = half ? nl0 : 0, lv1 = half ? cfg.n_levels : nl0;
     float lacc = 0.0f;
     bool first = true;
+    // Deferred grid scatter (2-feature grids): a tile's encoder gradient of
+    // this thread's eight levels (pdg, two columns per level, the next
+    // level's first) and the sample position wait for the next tile, whose
+    // eight MMA waits each issue one level's atomics: the L2 atomics then
+    // overlap the tensor-core work instead of following it.
+    float pdg[16];
+    float px = 0.0f, py = 0.0f, pz = 0.0f;
+    bool pend = false;
+    int pq = 0;  // pending levels already issued
+    auto scatter_next = [&]() {
+        if (F2 && pend && pq < 8) {
+            const int l = 8 * half + pq;
+            if (l < cfg.n_levels) {
+                const Cell cl = make_cell(px, py, pz, cfg.level_res[l]);
+                float* gl = grad + (size_t)cfg.level_off[l] * 2;
+                uint32_t idx[8];
+                float ws[8];
+                corners8(cfg, l, cl, idx, ws);
+#pragma unroll
+                for (int c = 0; c < 8; c += 2)
+                    scatter_pair2(gl, cfg.level_off[l], idx[c], idx[c + 1], ws[c], ws[c + 1], pdg[0], pdg[1]);
+            }
+#pragma unroll
+            for (int i = 0; i < 14; ++i) pdg[i] = pdg[i + 2];
+            ++pq;
+        }
+    };
     const int64_t ntiles = (n + kTile - 1) / kTile;
     for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
         const int64_t j = tile * kTile + row;
@@ -1034,6 +1061,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(
                 }
                 mma_commit(bar_mma);
             }
+            scatter_next();  // the previous tile's grid gradient, one level
             // Warp 0 spins on the barrier; the others sleep at the CTA
             // barrier, which then orders their TMEM reads after completion.
             const bool done = warp != 0 || mbar_wait_bounded(bar_mma, phase);
@@ -1129,6 +1157,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(
                 }
                 mma_commit(bar_mma);
             }
+            scatter_next();
             const bool done = warp != 0 || mbar_wait_bounded(bar_mma, phase);
             phase ^= 1u;
             ok = !__syncthreads_or(!done);
@@ -1168,7 +1197,18 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(
                     for (int i = 0; i < 16; ++i) dg[i] = __uint_as_float(r[i]);
                 }
                 tc_fence_before();
-                if (valid) {
+                if constexpr (F2) {
+                    while (pend && pq < 8) scatter_next();  // networks with fewer than 4 layers
+                    pend = valid;
+                    pq = 0;
+                    if (valid) {
+                        px = pos[j];
+                        py = pos[ld + j];
+                        pz = pos[2 * ld + j];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) pdg[i] = dg[i];
+                    }
+                } else if (valid) {
                     const float x = pos[j], y = pos[ld + j], z = pos[2 * ld + j];
                     const int F = cfg.feat;
                     if (F == 2) scatter_levels<2, 8>(cfg, grad, x, y, z, 8 * half, dg);
@@ -1182,6 +1222,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(
         }
         first = false;
     }
+    while (pend && pq < 8) scatter_next();  // the last tile's grid gradient
     // Loss: one atomic per warp.
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lacc += __shfl_xor_sync(0xffffffffu, lacc, o);
