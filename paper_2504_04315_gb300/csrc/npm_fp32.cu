@@ -1145,18 +1145,15 @@ static cudaError_t launch_fwd_inst(const DevCfg& cfg, const float* grid, const f
     int G = (int)((227 * 1024 - wbytes) / gbytes);
     if (G > fwd_max_groups(I)) G = fwd_max_groups(I);
     // Tuning override (groups per CTA) for launch-configuration sweeps.
-    if (const char* env = getenv("NPM_FP32_GROUPS")) {
-        const int g = atoi(env);
-        if (g >= 1 && g < G) G = g;
-    }
+    static std::atomic<int> env_groups{INT32_MIN + 1};
+    const int og = env_override("NPM_FP32_GROUPS", env_groups);
+    if (og >= 1 && og < G) G = og;
     if (G < 1) return cudaErrorInvalidConfiguration;
     const size_t smem = wbytes + G * gbytes;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     // Carve out only the shared memory this CTA needs; the rest of the
     // 256 KB stays L1 for the grid gathers.
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             carveout_percent(smem + 1024));
+    static std::atomic<uint64_t> attrs{~0ull};
+    cudaError_t e = set_smem_attrs(kern, smem, carveout_percent(smem + 1024), attrs);
     if (e != cudaSuccess) return e;
     int64_t g = sm_count();
     const int64_t need = (tiles_hint + G - 1) / G;
@@ -1184,10 +1181,8 @@ static cudaError_t launch_fwd_ws(const DevCfg& cfg, const float* grid, const flo
                                  cudaStream_t st) {
     auto kern = k_forward_fp32_ws<SAMPLE, 4, 4, GC, kWsDepth>;
     const size_t smem = ws_smem_bytes(cfg, 4, GC);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             carveout_percent(smem + 1024));
+    static std::atomic<uint64_t> attrs{~0ull};
+    cudaError_t e = set_smem_attrs(kern, smem, carveout_percent(smem + 1024), attrs);
     if (e != cudaSuccess) return e;
     int64_t g = sm_count();
     const int64_t need = (tiles_hint + GC - 1) / GC;
@@ -1202,8 +1197,9 @@ static cudaError_t launch_fwd_ws(const DevCfg& cfg, const float* grid, const flo
 // NPM_FP32_WS (0, 3 or 4) overrides the choice for launch sweeps.
 static int ws_groups(const DevCfg& cfg, int inst) {
     // three consumer groups at 128 registers beat four at 96 (measured)
-    int gc = 3;
-    if (const char* env = getenv("NPM_FP32_WS")) gc = atoi(env);
+    static std::atomic<int> env_ws{INT32_MIN + 1};
+    const int ov = env_override("NPM_FP32_WS", env_ws);
+    const int gc = ov == INT32_MIN ? 3 : ov;
     if (gc != 3 && gc != 4) return 0;
     if (inst != 4 || (cfg.K + 1) / 2 > 4) return 0;
     if (ws_smem_bytes(cfg, 4, gc) > 227 * 1024) return 0;

@@ -4,10 +4,44 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
+
+#include <atomic>
 
 #include "npm_device.cuh"
 
 namespace npm {
+
+// Dynamic shared-memory limit and L1/shared carveout of a kernel, set only
+// when (device, size, carveout) differs from the last call for that kernel
+// (`last` is the caller's per-kernel cache): the attribute calls cost host
+// time that small, latency-bound launches would otherwise pay every time.
+template <typename KernelT>
+inline cudaError_t set_smem_attrs(KernelT kern, size_t smem, int carveout_pct, std::atomic<uint64_t>& last) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t key = ((uint64_t)(unsigned)dev << 40) | ((uint64_t)(unsigned)carveout_pct << 32) | (uint64_t)smem;
+    if (last.load(std::memory_order_relaxed) == key) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carveout_pct);
+    if (e != cudaSuccess) return e;
+    last.store(key, std::memory_order_relaxed);
+    return cudaSuccess;
+}
+
+// Integer tuning override from the environment, read once per process
+// (`cache` holds it; INT32_MIN when unset or not a number).
+inline int env_override(const char* name, std::atomic<int>& cache) {
+    int v = cache.load(std::memory_order_relaxed);
+    if (v == INT32_MIN + 1) {
+        const char* s = getenv(name);
+        v = (s && *s) ? atoi(s) : INT32_MIN;
+        cache.store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
 
 // Default bound of a kernel-internal wait: 2^31 SM clock cycles (about a
 // second at 2 GHz).

@@ -1413,26 +1413,31 @@ template <int KMAX, bool F2, int NL>
 static cudaError_t launch_tc(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStream_t st) {
     TcState* s = h->tc;
     auto kern = k_forward_tc<KMAX, F2, NL>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem);
-    if (e != cudaSuccess) return e;
-    // CTAs per SM from registers and tensor memory; then carve out just the
-    // shared memory they need so the rest stays L1 for the grid gathers.
-    cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, kern);
-    if (e != cudaSuccess) return e;
-    const int regs_cta = ((fa.numRegs + 7) / 8 * 8) * kThreads;
+    // CTAs per SM from registers (the instance's count, queried once) and
+    // tensor memory; then carve out just the shared memory they need so the
+    // rest stays L1 for the grid gathers.
+    static std::atomic<int> regs{-1};
+    int nregs = regs.load(std::memory_order_relaxed);
+    if (nregs < 0) {
+        cudaFuncAttributes fa;
+        cudaError_t ea = cudaFuncGetAttributes(&fa, kern);
+        if (ea != cudaSuccess) return ea;
+        nregs = fa.numRegs;
+        regs.store(nregs, std::memory_order_relaxed);
+    }
+    const int regs_cta = ((nregs + 7) / 8 * 8) * kThreads;
     int per_sm = regs_cta > 0 ? 65536 / regs_cta : 1;
     const int tmem_cap = (int)(512u / s->cfg.tmem_cols);
     if (per_sm > tmem_cap) per_sm = tmem_cap;
     if (per_sm > 16) per_sm = 16;
     while (per_sm > 1 && (size_t)per_sm * (s->smem + 1024) > 227 * 1024) --per_sm;
-    if (const char* env = getenv("NPM_TC_CTAS_PER_SM")) {
-        const int v = atoi(env);
-        if (v >= 1 && v < per_sm) per_sm = v;
-    }
+    static std::atomic<int> env_ctas{INT32_MIN + 1};
+    const int v = env_override("NPM_TC_CTAS_PER_SM", env_ctas);
+    if (v >= 1 && v < per_sm) per_sm = v;
     if (per_sm < 1) per_sm = 1;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             carveout_percent((size_t)per_sm * (s->smem + 1024)));
+    static std::atomic<uint64_t> attrs{~0ull};
+    cudaError_t e = set_smem_attrs(kern, s->smem, carveout_percent((size_t)per_sm * (s->smem + 1024)), attrs);
+    if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1457,10 +1462,8 @@ static cudaError_t launch_train_tc(npm_handle* h, int64_t n, int64_t ld, const f
                                    float* loss, cudaStream_t st) {
     TcState* s = h->tc;
     auto kern = k_train_tc<KMAX, F2>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->train.smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             carveout_percent(s->train.smem + 1024));
+    static std::atomic<uint64_t> attrs{~0ull};
+    cudaError_t e = set_smem_attrs(kern, s->train.smem, carveout_percent(s->train.smem + 1024), attrs);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -1472,8 +1475,8 @@ static cudaError_t launch_train_tc(npm_handle* h, int64_t n, int64_t ld, const f
     if (F2 && s->enc && n <= h->cfg.max_batch) {
         // Levels per thread: two (64 registers, more warps) measured a little
         // faster than four; tuning override NPM_ENC_LPT (2 or 4).
-        int lpt = 2;
-        if (const char* env = getenv("NPM_ENC_LPT")) lpt = atoi(env) == 4 ? 4 : 2;
+        static std::atomic<int> env_lpt{INT32_MIN + 1};
+        const int lpt = env_override("NPM_ENC_LPT", env_lpt) == 4 ? 4 : 2;
         const int64_t items = n * ((h->dc.n_levels + lpt - 1) / lpt);
         int64_t eg = (items + 255) / 256;
         if (eg > (int64_t)sms * 16) eg = (int64_t)sms * 16;
