@@ -420,6 +420,22 @@ npm_status npm_load(npm_handle* h, const char* path);
  * wait timeouts). Synchronises the stream. */
 npm_status npm_check_device_status(npm_handle* h, void* stream);
 
+/* Validation (not a hot call): for each of n_pos positions x_p (pos
+ * [3][ld], aux [7][ld] in product mode, device memory), the integral over
+ * the sphere of the mixture density, I_p = sum_k weights[k] V(dirs_k | x_p),
+ * by the caller's quadrature (dirs [3][n_dir] unit vectors and weights
+ * [n_dir] doubles, device memory, e.g. Gauss-Legendre in cos(theta) times
+ * uniform in phi). V is a density on the sphere (Eq. 3-4), so I_p = 1 up to
+ * the quadrature and the density's own rounding. The densities come from
+ * npm_eval_pdf (the same kernels as every query); the weighted sums are
+ * reduced on the GPU in FP64. out [n_pos] doubles, device memory. Works in
+ * chunks through the handle's staging buffers (no allocation), so it must
+ * not overlap npm_query_sample_host on the same handle. Asynchronous.
+ * Errors: NPM_ERR_INVALID_ARG, NPM_ERR_CAPACITY (n_dir > max_batch). */
+npm_status npm_pdf_integral(npm_handle* h, int64_t n_pos, const float* pos, const float* aux, int64_t ld,
+                            int64_t n_dir, const float* dirs, const double* weights, double* out,
+                            void* stream);
+
 /* Bound of the device-side waits inside the FP32 forward kernel of this
  * handle (its encoder and MLP thread groups hand tiles over through
  * shared-memory mailboxes; failure handling, not part of the method).

@@ -242,6 +242,20 @@ class NPM:
         _lib.check(self._L.npm_check_device_status(self._h, _stream_ptr(stream)),
                    "npm_check_device_status")
 
+    def pdf_integral(self, pos, dirs, weights, aux=None, stream=None):
+        """Integral over the sphere of the mixture density at each position
+        (npm_pdf_integral): sum_k weights[k] V(dirs[:, k] | pos[:, p]),
+        reduced in FP64 on the GPU. pos [3][n] (and aux [7][n]) float32,
+        dirs [3][n_dir] float32, weights [n_dir] float64, device tensors;
+        returns a float64 device tensor [n]."""
+        import torch
+        n, n_dir = pos.shape[1], dirs.shape[1]
+        out = torch.empty((n,), dtype=torch.float64, device=pos.device)
+        _lib.check(self._L.npm_pdf_integral(
+            self._h, n, _ptr(pos), _ptr(aux) if aux is not None else None, pos.stride(0), n_dir,
+            _ptr(dirs), _ptr(weights), _ptr(out), _stream_ptr(stream)), "npm_pdf_integral")
+        return out
+
     def set_wait_limit(self, cycles: int):
         """Bound (SM clock cycles) of the FP32 forward kernel's internal
         waits (npm_set_wait_limit); <= 0 makes each wait one test."""

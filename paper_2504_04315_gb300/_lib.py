@@ -97,6 +97,7 @@ SIGNATURES = {
     "npm_load": (st, [vp, C.c_char_p]),
     "npm_check_device_status": (st, [vp, vp]),
     "npm_set_wait_limit": (st, [vp, i64]),
+    "npm_pdf_integral": (st, [vp, i64, vp, vp, i64, i64, vp, vp, vp, vp]),
     "npm_last_error": (C.c_char_p, []),
     "npm_wavefront_create": (st, [vp, C.POINTER(NpmFrameConfig), C.POINTER(vp)]),
     "npm_wavefront_run": (st, [vp, C.c_int, vp, C.POINTER(NpmFrameStats)]),
