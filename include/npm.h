@@ -371,6 +371,16 @@ npm_status npm_get_params(npm_handle* h, float* host, int64_t count);
  * npm_backward; npm_adam_step and npm_train_step leave it zeroed). */
 npm_status npm_get_grads(npm_handle* h, float* host, int64_t count);
 
+/* Device-memory forms of npm_set_params / npm_get_grads, ordered on
+ * `stream` and not synchronising (for differentiable wrappers that keep the
+ * parameters in a framework's device tensor). dev: npm_num_params FP32
+ * values in the same public layout, DEVICE memory, owned by the caller.
+ * set also refreshes the reduced-precision and padded copies (and restarts
+ * the weight average, as npm_set_params does). Errors: NPM_ERR_INVALID_ARG
+ * (NULL or a count other than npm_num_params), NPM_ERR_CUDA. */
+npm_status npm_set_params_device(npm_handle* h, const float* dev, int64_t count, void* stream);
+npm_status npm_get_grads_device(npm_handle* h, float* dev, int64_t count, void* stream);
+
 /* Device pointers to the FP32 master parameters and gradient (owned by the
  * handle, valid until npm_destroy). */
 float* npm_params_device(npm_handle* h);

@@ -197,6 +197,24 @@ class NPM:
                    "npm_get_grads")
         return a
 
+    def set_params_device(self, theta, stream=None):
+        """Parameters from a float32 CUDA tensor [npm_num_params] in the
+        public layout (npm_set_params_device; stream-ordered)."""
+        torch = _torch()
+        if theta.dtype != torch.float32 or not theta.is_cuda or not theta.is_contiguous():
+            raise TypeError("theta must be a contiguous float32 CUDA tensor")
+        _lib.check(self._L.npm_set_params_device(self._h, _ptr(theta), theta.numel(), _stream_ptr(stream)),
+                   "npm_set_params_device")
+
+    def grads_device(self, out=None, stream=None):
+        """The gradient buffer as a float32 CUDA tensor in the public layout
+        (npm_get_grads_device; stream-ordered)."""
+        torch = _torch()
+        g = torch.empty((self.num_params(),), dtype=torch.float32, device="cuda") if out is None else out
+        _lib.check(self._L.npm_get_grads_device(self._h, _ptr(g), g.numel(), _stream_ptr(stream)),
+                   "npm_get_grads_device")
+        return g
+
     def set_ema(self, decay: float, stream=None):
         """Inference evaluates the moving average of the weights (npm_set_ema);
         decay 0 turns it off."""
@@ -260,6 +278,53 @@ class NPM:
         """Bound (SM clock cycles) of the FP32 forward kernel's internal
         waits (npm_set_wait_limit); <= 0 makes each wait one test."""
         _lib.check(self._L.npm_set_wait_limit(self._h, int(cycles)), "npm_set_wait_limit")
+
+
+def _make_log_density():
+    torch = _torch()
+
+    class LogDensity(torch.autograd.Function):
+        """log V(dir_j | Theta(x_j); theta) for a batch, differentiable in the
+        parameters theta (float32 CUDA tensor [npm_num_params], public layout).
+
+        Forward loads theta into the model (npm_set_params_device) and
+        evaluates the density with the library's kernels (npm_eval_pdf);
+        backward reloads theta and runs the hand-written backward
+        (npm_backward: decode, MLP and grid, activations recomputed, with the
+        incoming gradient as the per-query weight of d log V), returning the
+        parameter gradient (npm_get_grads_device). Only the elementwise log
+        of the density runs outside the library."""
+
+        @staticmethod
+        def forward(ctx, theta, model, pos, dirs, aux=None):
+            model.set_params_device(theta)
+            v = model.eval_pdf(pos, dirs, aux)
+            n = pos.shape[1]
+            ctx.model = model
+            ctx.save_for_backward(theta, pos, dirs, aux if aux is not None else theta.new_empty(0))
+            ctx.has_aux = aux is not None
+            return torch.log(v[:n])
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            theta, pos, dirs, aux = ctx.saved_tensors
+            model = ctx.model
+            model.set_params_device(theta)
+            model.backward(pos, dirs, grad_out.contiguous().to(torch.float32), aux if ctx.has_aux else None)
+            return model.grads_device(), None, None, None, None
+
+    return LogDensity
+
+
+_LOG_DENSITY = None
+
+
+def log_density(theta, model, pos, dirs, aux=None):
+    """Differentiable log V (LogDensity.apply): see _make_log_density."""
+    global _LOG_DENSITY
+    if _LOG_DENSITY is None:
+        _LOG_DENSITY = _make_log_density()
+    return _LOG_DENSITY.apply(theta, model, pos, dirs, aux)
 
 
 class Server:

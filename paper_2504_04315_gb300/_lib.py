@@ -86,6 +86,8 @@ SIGNATURES = {
     "npm_set_params": (st, [vp, vp, i64]),
     "npm_get_params": (st, [vp, vp, i64]),
     "npm_get_grads": (st, [vp, vp, i64]),
+    "npm_set_params_device": (st, [vp, vp, i64, vp]),
+    "npm_get_grads_device": (st, [vp, vp, i64, vp]),
     "npm_params_device": (vp, [vp]),
     "npm_grads_device": (vp, [vp]),
     "npm_set_ema": (st, [vp, f32, vp]),

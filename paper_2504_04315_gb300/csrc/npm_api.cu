@@ -332,6 +332,31 @@ npm_status npm_get_params(npm_handle* h, float* host, int64_t count) {
     return copy_public(h, h ? h->params : nullptr, host, count, false);
 }
 
+npm_status npm_set_params_device(npm_handle* h, const float* dev, int64_t count, void* stream) {
+    if (!h || !dev) return fail(NPM_ERR_INVALID_ARG, "NULL argument");
+    if (count != h->ng + h->nmlp) return fail(NPM_ERR_INVALID_ARG, "count != npm_num_params");
+    cudaStream_t st = (cudaStream_t)stream;
+    NPM_CUDA(cudaMemcpyAsync(h->params, dev, h->ng * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy grid");
+    NPM_CUDA(cudaMemcpyAsync(h->params + h->mlp_off, dev + h->ng, h->nmlp * sizeof(float),
+                             cudaMemcpyDeviceToDevice, st),
+             "copy mlp");
+    if (h->ema)
+        NPM_CUDA(cudaMemcpyAsync(h->ema, h->params, h->n_int * sizeof(float), cudaMemcpyDeviceToDevice, st),
+                 "reset ema");
+    return refresh_derived(h, st);
+}
+
+npm_status npm_get_grads_device(npm_handle* h, float* dev, int64_t count, void* stream) {
+    if (!h || !dev) return fail(NPM_ERR_INVALID_ARG, "NULL argument");
+    if (count != h->ng + h->nmlp) return fail(NPM_ERR_INVALID_ARG, "count != npm_num_params");
+    cudaStream_t st = (cudaStream_t)stream;
+    NPM_CUDA(cudaMemcpyAsync(dev, h->grads, h->ng * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy grid");
+    NPM_CUDA(cudaMemcpyAsync(dev + h->ng, h->grads + h->mlp_off, h->nmlp * sizeof(float),
+                             cudaMemcpyDeviceToDevice, st),
+             "copy mlp");
+    return NPM_OK;
+}
+
 npm_status npm_set_ema(npm_handle* h, float decay, void* stream) {
     if (!h) return fail(NPM_ERR_INVALID_ARG, "handle is NULL");
     if (!(decay >= 0.0f && decay < 1.0f)) return fail(NPM_ERR_INVALID_ARG, "decay must be in [0, 1)");
