@@ -447,6 +447,35 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
 
 // --------------------------------------------------------------- decode
 
+// Sampler of the reduced-precision path (Sec. 5.3, Jakob's inversion as in
+// vmf_sample) on the hardware approximations: 1 - e^{-2k} and log(1 + y) by
+// their series where the direct forms lose relative accuracy (2k < 0.1,
+// |y| < 1e-2; truncation below 1e-6 relative), the fast exponential,
+// logarithm and divide elsewhere, and sqrt as x rsqrt(x). The density is
+// always evaluated at the direction returned, so its accuracy bar does not
+// depend on these approximations.
+__device__ __forceinline__ void vmf_sample_rp(const Lobe& L, float u1, float u2, float out[3]) {
+    const float k = L.kap;
+    const float x = 2.0f * k;
+    const float em1 = x < 0.1f ? -x * (1.0f - x * (0.5f - x * (1.0f / 6.0f - x * (1.0f / 24.0f))))
+                               : __expf(-x) - 1.0f;  // e^{-2k} - 1
+    const float y = u1 * em1;                        // in (-1, 0]
+    const float l1p = fabsf(y) < 1e-2f ? y * (1.0f - y * (0.5f - y * (1.0f / 3.0f - y * 0.25f)))
+                                       : __logf(1.0f + y);
+    float t1 = k > 1e-20f ? __fdividef(-l1p, k) : 2.0f * u1;
+    t1 = fminf(fmaxf(t1, 0.0f), 2.0f);
+    const float W = 1.0f - t1;
+    const float q = t1 * (2.0f - t1);
+    const float sn = q > 0.0f ? q * rsqrtf(q) : 0.0f;
+    float sp, cp;
+    __sincosf(2.0f * kPi * (u2 - 0.5f), &sp, &cp);
+    const float lx = -sn * cp, ly = -sn * sp;
+    float tt[3], bb[3];
+    frame(L.mu, tt, bb);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out[a] = lx * tt[a] + ly * bb[a] + W * L.mu[a];
+}
+
 // KEXACT: the model has exactly KMAX lobes (no per-lobe bound checks).
 template <int KMAX, bool KEXACT>
 __device__ __forceinline__ void tc_decode(const TcCfg& tc, const float (&raw)[4 * KMAX], int64_t j,
@@ -514,7 +543,7 @@ __device__ __forceinline__ void tc_decode(const TcCfg& tc, const float (&raw)[4 
 #pragma unroll
             for (int i = 1; i < KMAX; ++i)
                 if (i == sel) sl = lob[i];
-            vmf_sample(sl, u1, u2, w);
+            vmf_sample_rp(sl, u1, u2, w);
         }
     } else if (valid) {
         w[0] = uin[j];
@@ -621,6 +650,29 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? 6 : (KMAX == 8 
         const int64_t ld = S.ld;
         const int64_t j = (tile - S.tile0) * kTile + t;
         const bool valid = j < n;
+        // Into L2 while this tile is encoded and run through the MLP: its
+        // uniforms (or directions), which the decode reads last, and the
+        // next tile's positions. Lane l of warp 3 takes row l >> 2 (0-3:
+        // uniforms, 4-6: next positions), quarter l & 3 (128 bytes) of the
+        // 512-byte rows.
+        if (warp == 3) {
+            const int lane = t & 31, r = lane >> 2;
+            const int64_t b0 = (tile - S.tile0) * kTile + 32 * (lane & 3);
+            if (r < 4) {
+                if ((r < 3 || S.ufrac > 0.0f) && b0 < n)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(S.uin + r * ld + b0));
+            } else if (r < 7) {
+                const int64_t nt = tile + gridDim.x;
+                if (nt < ntiles) {
+                    int s2 = sg;
+                    while (s2 + 1 < qb.nseg && nt >= qb.seg[s2 + 1].tile0) ++s2;
+                    const QuerySeg& S2 = qb.seg[s2];
+                    const int64_t b2 = (nt - S2.tile0) * kTile + 32 * (lane & 3);
+                    const int64_t n2 = (s2 == 0 && qb.n_dev) ? n0 : S2.n;
+                    if (b2 < n2) asm volatile("prefetch.global.L2 [%0];" ::"l"(S2.pos + (r - 4) * S2.ld + b2));
+                }
+            }
+        }
         tc_encode<F2>(tc, grid_h, j, valid, ld, S.pos, S.aux, sA0, t, tc.split ? a0_lo : 0u, false, 0,
                       tc.base.n_levels, true);
         fence_async_smem();
