@@ -127,7 +127,7 @@ def mlp_flops(w):
 
 # DRAM bytes of one k_forward_fp32_ws launch on the paper-shaped workload
 # (2^20 queries) from the ncu capture summarised in profiles/.
-FP32_FORWARD_DRAM_BYTES = 66750720 + 8851968
+FP32_FORWARD_DRAM_BYTES = 66753024 + 8907520
 
 # Algorithmic work per query of the tensor-core forward on the tiny model
 # (K = 4): transcendentals of the vMF decode, sample and pdf (softmax 4,
