@@ -463,8 +463,12 @@ npm_status npm_query_sample_host(npm_handle* h, int64_t n, const float* pos, con
     float* dpdf = ddir + 3 * mb;
     const int urows = uniform_frac > 0.0f ? 4 : 3;
     const int arows = h->cfg.mode == NPM_PRODUCT ? 7 : 0;
-    // Chunks of at least 2^16 queries, at most 8 of them.
-    int64_t chunk = n / 8;
+    // Chunks of at least 2^16 queries, four of them by default (measured
+    // best for 2^20 queries: fewer expose more of the first and last copies,
+    // more pay more kernel ramp-up and tail); NPM_HOST_CHUNKS overrides.
+    static std::atomic<int> env_chunks{INT32_MIN + 1};
+    const int nch = npm::env_override("NPM_HOST_CHUNKS", env_chunks);
+    int64_t chunk = n / (nch >= 1 && nch <= 64 ? nch : 4);
     if (chunk < 65536) chunk = 65536;
     NPM_CUDA(cudaEventRecord(h->ev[0], user), "record");
     for (int i = 0; i < 2; ++i) NPM_CUDA(cudaStreamWaitEvent(h->side[i], h->ev[0], 0), "wait");
@@ -473,21 +477,21 @@ npm_status npm_query_sample_host(npm_handle* h, int64_t n, const float* pos, con
         const int64_t cn = n - c0 < chunk ? n - c0 : chunk;
         cudaStream_t st = h->side[c & 1];
         const size_t bytes = (size_t)cn * sizeof(float);
-        for (int r = 0; r < 3; ++r)
-            NPM_CUDA(cudaMemcpyAsync(dpos + r * mb + c0, pos + r * ld + c0, bytes,
-                                     cudaMemcpyHostToDevice, st), "copy pos");
-        for (int r = 0; r < arows; ++r)
-            NPM_CUDA(cudaMemcpyAsync(daux + r * mb + c0, aux + r * ld + c0, bytes,
-                                     cudaMemcpyHostToDevice, st), "copy aux");
-        for (int r = 0; r < urows; ++r)
-            NPM_CUDA(cudaMemcpyAsync(du + r * mb + c0, u + r * ld + c0, bytes,
-                                     cudaMemcpyHostToDevice, st), "copy u");
+        const size_t hp = (size_t)ld * sizeof(float), dp = (size_t)mb * sizeof(float);  // row pitches
+        // One strided copy per [rows][chunk] block (rows are ld apart on the
+        // host, mb apart on the device).
+        NPM_CUDA(cudaMemcpy2DAsync(dpos + c0, dp, pos + c0, hp, bytes, 3, cudaMemcpyHostToDevice, st),
+                 "copy pos");
+        if (arows)
+            NPM_CUDA(cudaMemcpy2DAsync(daux + c0, dp, aux + c0, hp, bytes, arows, cudaMemcpyHostToDevice, st),
+                     "copy aux");
+        NPM_CUDA(cudaMemcpy2DAsync(du + c0, dp, u + c0, hp, bytes, urows, cudaMemcpyHostToDevice, st),
+                 "copy u");
         s = npm_query_sample(h, cn, dpos + c0, arows ? daux + c0 : nullptr, du + c0, mb,
                              uniform_frac, ddir + c0, dpdf + c0, nullptr, st);
         if (s != NPM_OK) return s;
-        for (int r = 0; r < 3; ++r)
-            NPM_CUDA(cudaMemcpyAsync(dir_out + r * ld + c0, ddir + r * mb + c0, bytes,
-                                     cudaMemcpyDeviceToHost, st), "copy dir");
+        NPM_CUDA(cudaMemcpy2DAsync(dir_out + c0, hp, ddir + c0, dp, bytes, 3, cudaMemcpyDeviceToHost, st),
+                 "copy dir");
         NPM_CUDA(cudaMemcpyAsync(pdf_out + c0, dpdf + c0, bytes, cudaMemcpyDeviceToHost, st),
                  "copy pdf");
     }

@@ -274,3 +274,36 @@ def test_bounded_wait_timeout_is_reported_and_context_survives():
     pick = np.arange(0, n, 16)
     compare_samples(w, params, pos[:, pick], u[:, pick], None, 0.0, host(d)[:, pick], host(p)[pick],
                     PDF_RTOL_FP32, DIR_TOL_FP32, MARGIN_FP32)
+
+
+@pytest.mark.parametrize("w,n,ld,alpha", [(synth.PAPER_HASH, 200_003, 200_064, 0.0),
+                                          (PRODUCT_SMALL, 70_001, 70_001, 0.5)],
+                         ids=["paper-hash", "product-uniform-branch"])
+def test_query_sample_host_buffers_match_device(w, n, ld, alpha):
+    # The end-to-end entry point (pinned host buffers, strided chunk copies
+    # on two internal streams) returns exactly what the device entry point
+    # returns for the same inputs: per-query results do not depend on the
+    # chunking. Several chunks, a ragged tail and ld > n; columns beyond n
+    # of the host outputs stay untouched.
+    params = synth.random_params(w, 31)
+    pos = np.zeros((3, ld), np.float32)
+    pos[:, :n] = synth.positions(31, n)
+    u = np.zeros((4, ld), np.float32)
+    u[:, :n] = synth.sample_uniforms(31, n, rows=4)
+    aux = None
+    if w.mode == synth.PRODUCT:
+        aux = np.zeros((7, ld), np.float32)
+        aux[:, :n] = synth.aux_inputs(31, n)
+    m = make_model(w, params, ld)
+    d_dev, p_dev, _ = m.query_sample(cuda(pos), cuda(u), None if aux is None else cuda(aux),
+                                     uniform_frac=alpha, n=n)
+    hpos = torch.from_numpy(pos).pin_memory()
+    hu = torch.from_numpy(u).pin_memory()
+    haux = None if aux is None else torch.from_numpy(aux).pin_memory()
+    hd = torch.full((3, ld), -7.0).pin_memory()
+    hp = torch.full((ld,), -7.0).pin_memory()
+    m.query_sample_host(hpos, hu, hd, hp, haux, uniform_frac=alpha, n=n)
+    m.check_device_status()
+    assert np.array_equal(hd.numpy()[:, :n], host(d_dev)[:, :n])
+    assert np.array_equal(hp.numpy()[:n], host(p_dev)[:n])
+    assert np.all(hd.numpy()[:, n:] == -7.0) and np.all(hp.numpy()[n:] == -7.0)
