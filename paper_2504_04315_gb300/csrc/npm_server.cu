@@ -160,10 +160,15 @@ cudaEvent_t take_event(npm_server* s) {
     return e;
 }
 
+// rows x n block between [rows][ld] layouts: one strided copy (the worker
+// thread's API calls per request are what a busy server pays for).
 void copy_rows(float* dst, int64_t dst_ld, const float* src, int64_t src_ld, int rows, int64_t n,
                cudaMemcpyKind kind, cudaStream_t st) {
-    for (int r = 0; r < rows; ++r)
-        cudaMemcpyAsync(dst + r * dst_ld, src + r * src_ld, (size_t)n * sizeof(float), kind, st);
+    if (rows == 1)
+        cudaMemcpyAsync(dst, src, (size_t)n * sizeof(float), kind, st);
+    else
+        cudaMemcpy2DAsync(dst, (size_t)dst_ld * sizeof(float), src, (size_t)src_ld * sizeof(float),
+                          (size_t)n * sizeof(float), rows, kind, st);
 }
 
 // Launches one batch (called by the worker without the lock held).
