@@ -542,8 +542,11 @@ static npm_status adam_impl(npm_handle* h, const float* loss, cudaStream_t st) {
                               h->cfg.beta1, h->cfg.beta2, h->cfg.eps, step_dev(h), loss, status,
                               h->grid_h, h->grid_h ? (h->ng / 4) * 4 : 0, h->ema, h->ema_decay, st),
              "adam launch");
-    if (h->grid_h && h->ng % 4)
-        NPM_CUDA(npm::launch_to_half(h->ng, inf_params(h), h->grid_h, st), "grid fp16 tail");
+    if (h->grid_h && h->ng % 4) {
+        // The last ng % 4 entries, beyond the Adam kernel's float4 lanes.
+        const int64_t b = (h->ng / 4) * 4;
+        NPM_CUDA(npm::launch_to_half(h->ng - b, inf_params(h) + b, h->grid_h + b, st), "grid fp16 tail");
+    }
     NPM_CUDA(npm::launch_arrange_weights(h->dc, h->params + h->mlp_off, h->wfwd, h->wbwd, st),
              "arrange weights");
     npm_status s = arrange_inference_weights(h, st);
