@@ -292,10 +292,10 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
     }
     const int F = F2 ? 2 : cfg.feat;
     int l = lbeg;
-    if (!F2 && (F == 4 || F == 8) && lbeg == 0 && lend == 1 && tail && !pad_all &&
-        cfg.mode != NPM_PRODUCT) {
+    if (!F2 && (F == 4 || F == 8) && lbeg == 0 && lend == 1 && tail && cfg.mode != NPM_PRODUCT) {
         // A single level of 4 or 8 features fills the first 8-column chunk
-        // (features, then zeros): one 16-byte store (and one for residuals).
+        // (features, then zeros): one 16-byte store (and one for residuals);
+        // with pad_all, zero chunks follow up to kp.
         const Cell cl = make_cell(x, y, z, cfg.level_res[0]);
         uint32_t idx[8];
         corner_idx8(cfg, 0, cl, idx);
@@ -334,6 +334,12 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
         const uint32_t off = tile_off(row, 0, kp);
         *reinterpret_cast<uint4*>(sA + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
         if (lo) *reinterpret_cast<uint4*>(sA + lo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        if (pad_all)
+            for (int c = 8; c < kp; c += 8) {
+                const uint32_t oz = tile_off(row, c, kp);
+                *reinterpret_cast<uint4*>(sA + oz) = make_uint4(0u, 0u, 0u, 0u);
+                if (lo) *reinterpret_cast<uint4*>(sA + lo + oz) = make_uint4(0u, 0u, 0u, 0u);
+            }
         return;
     }
     if constexpr (F2) {
@@ -571,7 +577,7 @@ __device__ __forceinline__ void tc_decode(const TcCfg& tc, const float (&raw)[4 
 // layers, output chunks and lobes unrolled at compile time); NL = 0: any
 // layer count and K <= KMAX.
 template <int KMAX, bool F2, int NL>
-__global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? 6 : (KMAX == 8 ? 3 : 1)) k_forward_tc(const __grid_constant__ TcCfg tc,
+__global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 6) : (KMAX == 8 ? 3 : 1)) k_forward_tc(const __grid_constant__ TcCfg tc,
                                                          const __half* __restrict__ grid_h,
                                                          const uint8_t* __restrict__ wblob,
                                                          const __grid_constant__ QueryBatch qb,
@@ -673,7 +679,9 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? 6 : (KMAX == 8 
                 }
             }
         }
-        tc_encode<F2>(tc, grid_h, j, valid, ld, S.pos, S.aux, sA0, t, tc.split ? a0_lo : 0u, false, 0,
+        // Without a layer-0 buffer of its own the encoding also rewrites
+        // the zero chunks (the hidden layers reuse the buffer).
+        tc_encode<F2>(tc, grid_h, j, valid, ld, S.pos, S.aux, sA0, t, tc.split ? a0_lo : 0u, tc.a0_bytes == 0, 0,
                       tc.base.n_levels, true);
         fence_async_smem();
         tc_fence_before();
@@ -1356,7 +1364,11 @@ npm_status tc_create(npm_handle* h) {
     // zero chunks to write once; otherwise it shares the buffer of the
     // hidden layers (less shared memory, more L1 for the grid gathers).
     const int enc_width = c.n_levels * c.feat_per_level + (c.mode == NPM_PRODUCT ? 21 : 0);
-    const bool sep0 = (enc_width + 7) / 8 * 8 < t.layer[0].Kp;
+    // A single small grid level (the tiny models) shares the buffer anyway:
+    // its zero chunk costs one store per tile, and the smaller CTA lets eight
+    // of them share an SM instead of six.
+    const bool single_small = c.n_levels == 1 && c.feat_per_level <= 8 && c.mode != NPM_PRODUCT;
+    const bool sep0 = (enc_width + 7) / 8 * 8 < t.layer[0].Kp && !single_small;
     int maxkp1 = 16;  // widest input of the layers sharing the buffer
     for (int l = sep0 ? 1 : 0; l < c.n_layers; ++l) maxkp1 = std::max(maxkp1, t.layer[l].Kp);
     t.a_bytes = (uint32_t)(kTile * maxkp1 * 2);
