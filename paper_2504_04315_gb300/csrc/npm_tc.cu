@@ -751,7 +751,17 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 
             for (int i = 0; i < 16; ++i) rawf[c * 16 + i] = __uint_as_float(raw[c][i]);
         tc_decode<KMAX, (NL > 0)>(tc, rawf, j, valid, ld, S.uin, S.ufrac, qb.sample != 0, S.dir, S.pdf, S.mix);
     }
-    if (!ok && t == 0) atomicOr(status, kStatusTimeout);
+    if (!ok) {
+        if (t == 0) atomicOr(status, kStatusTimeout);
+        // Before the tensor memory is released: wait again, bounded, for this
+        // CTA's own asynchronous work that may still be in flight (the
+        // weights' bulk copy; the MMA batch whose wait gave up, the phase
+        // before `phase`).
+        if (warp == 0) {
+            (void)mbar_wait_bounded(bar_w, 0);
+            (void)mbar_wait_bounded(bar_mma, phase ^ 1u);
+        }
+    }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -1306,7 +1316,15 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(
             }
         }
     }
-    if (!ok && t == 0) atomicOr(status, kStatusTimeout);
+    if (!ok) {
+        if (t == 0) atomicOr(status, kStatusTimeout);
+        // As in the forward kernel: drain this CTA's in-flight weight copy and
+        // MMA batch (bounded) before the tensor memory is released.
+        if (warp == 0) {
+            (void)mbar_wait_bounded(bar_w, 0);
+            (void)mbar_wait_bounded(bar_mma, phase ^ 1u);
+        }
+    }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
