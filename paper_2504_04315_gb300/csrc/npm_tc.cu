@@ -1008,8 +1008,13 @@ __global__ void __launch_bounds__(256) k_train_encode(const __grid_constant__ De
     }
 }
 
+// The small four-lobe instance (single-level grids) is compiled for two
+// CTAs per SM (it fits 128 registers without spills): its tile chain of MMA
+// round trips is latency-bound, and a second CTA overlaps it.
+__host__ __device__ constexpr int train_ctas_per_sm(int kmax, bool f2) { return (kmax == 4 && !f2) ? 2 : 1; }
+
 template <int KMAX, bool F2>
-__global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(
+__global__ void __launch_bounds__(kTrainThreads, train_ctas_per_sm(KMAX, F2)) k_train_tc(
     const __grid_constant__ TcCfg tc, const __grid_constant__ TcTrain tt, const float* __restrict__ grid32,
     const uint8_t* __restrict__ wblob, int64_t n, int64_t ld, const float* __restrict__ pos,
     const float* __restrict__ aux, const float* __restrict__ dir, const float* __restrict__ rad,
@@ -1544,14 +1549,22 @@ static cudaError_t launch_train_tc(npm_handle* h, int64_t n, int64_t ld, const f
                                    float* loss, cudaStream_t st) {
     TcState* s = h->tc;
     auto kern = k_train_tc<KMAX, F2>;
+    // CTAs per SM: the instance's register budget, if shared and tensor
+    // memory hold that many.
+    int per_sm = train_ctas_per_sm(KMAX, F2);
+    while (per_sm > 1 && ((size_t)per_sm * (s->train.smem + 1024) > 227 * 1024 ||
+                          (uint32_t)per_sm * s->train.tmem_cols > 512u))
+        --per_sm;
     static std::atomic<uint64_t> attrs{~0ull};
-    cudaError_t e = set_smem_attrs(kern, s->train.smem, carveout_percent(s->train.smem + 1024), attrs);
+    cudaError_t e =
+        set_smem_attrs(kern, s->train.smem, carveout_percent((size_t)per_sm * (s->train.smem + 1024)), attrs);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t ntiles = (n + kTile - 1) / kTile;
-    const int g = (int)(ntiles < sms ? ntiles : sms);
+    const int64_t slots = (int64_t)per_sm * sms;
+    const int g = (int)(ntiles < slots ? ntiles : slots);
     int* status = reinterpret_cast<int*>(h->scalars + 8);
     const float* enc = nullptr;
     if (F2 && s->enc && n <= h->cfg.max_batch) {
