@@ -26,7 +26,6 @@
 
 namespace {
 
-constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 constexpr float kTwoPi = 6.28318530717958647692f;
 
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
@@ -40,8 +39,23 @@ __device__ __forceinline__ uint64_t key(uint64_t seed, uint64_t frame, uint64_t 
     return mix64(mix64(seed ^ (frame * 0x632BE59BD9B4E019ull)) ^ (bounce * 64 + what));
 }
 
+// 32-bit finaliser (two xor-multiply rounds; Wellons' "lowbias32" constants).
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// Uniform in [0, 1) with 24 random bits: element i of the stream keyed by
+// s0 (the driver's counters stay below 2^32). Two 32-bit hash rounds cost a
+// fraction of a 64-bit mix per draw, and the driver draws eight per path and
+// bounce.
 __device__ __forceinline__ float uni(uint64_t s0, uint64_t i) {
-    return (float)(mix64(s0 + (i + 1) * kGamma) >> 40) * (1.0f / 16777216.0f);
+    const uint32_t h = hash32(hash32((uint32_t)i + (uint32_t)s0) ^ (uint32_t)(s0 >> 32));
+    return (float)(h >> 8) * (1.0f / 16777216.0f);
 }
 
 __device__ __forceinline__ uint64_t globaltimer() {
@@ -114,9 +128,14 @@ __global__ void k_wf_start(WfState s) {
 }
 
 // Timestamp slot of the current frame, taken after every earlier kernel of
-// the stream has completed.
-__global__ void k_wf_stamp(WfState s, int slot) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) stamp(s, slot);
+// the stream has completed; clear >= 0 also zeroes that queue counter (the
+// next bounce's destination, which no later kernel reads before the next
+// advance appends to it).
+__global__ void k_wf_stamp(WfState s, int slot, int clear) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        stamp(s, slot);
+        if (clear >= 0) s.count[clear] = 0;
+    }
 }
 
 // Radiance estimate, training record, survival and compaction of one
@@ -171,10 +190,6 @@ __global__ void k_wf_advance(WfState s, int b, int src) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(s.queries, (unsigned long long)n);
 }
 
-__global__ void k_wf_clear(WfState s, int dst) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) s.count[dst] = 0;
-}
-
 __global__ void k_wf_end(WfState s) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         stamp(s, s.bounces + 1);
@@ -206,11 +221,10 @@ npm_status enqueue_frame(npm_wavefront* w, cudaStream_t st) {
     WfState& s = w->st;
     npm_handle* h = w->h;
     const int g = grid_for(s.P);
-    k_wf_start<<<g, 256, 0, st>>>(s);
-    k_wf_stamp<<<1, 32, 0, st>>>(s, 0);
+    k_wf_start<<<g, 256, 0, st>>>(s);  // also zeroes count[1]
+    k_wf_stamp<<<1, 32, 0, st>>>(s, 0, -1);
     for (int b = 0; b < s.bounces; ++b) {
         const int src = b & 1;
-        k_wf_clear<<<1, 32, 0, st>>>(s, src ^ 1);
         npm::QueryBatch qb;
         memset(&qb, 0, sizeof(qb));
         qb.nseg = 1;
@@ -228,7 +242,8 @@ npm_status enqueue_frame(npm_wavefront* w, cudaStream_t st) {
                               : npm::launch_forward_fp32_batch(h->dc, inf_params(h), inf_wfwd(h), qb, s.P, st, status_word(h), h->wait_limit);
         if (e != cudaSuccess) return npm::set_error(NPM_ERR_CUDA, cudaGetErrorString(e));
         k_wf_advance<<<g, 256, 0, st>>>(s, b, src);
-        k_wf_stamp<<<1, 32, 0, st>>>(s, 1 + b);
+        // count[src] was this bounce's queue: the next advance appends to it
+        k_wf_stamp<<<1, 32, 0, st>>>(s, 1 + b, src);
     }
     npm_status rs = npm_train_step(h, s.T, s.tpos, nullptr, s.tdir, s.trad, s.tpdf, s.T, w->loss, st);
     if (rs != NPM_OK) return rs;

@@ -61,15 +61,18 @@ def online_step(model: NPM, seed: int, n: int, uniform_frac: float = 0.5,
 
 
 def relative_variance(model: NPM, product: bool, seed: int, n: int, uniform: bool = False,
-                      fixed_position: Optional[float] = None, stream=None):
+                      fixed_position: Optional[float] = None, alpha: float = 0.0, stream=None):
     """Relative variance var(I) / mean(I)^2 of the one-sample estimator
     I = target(x, w) / pdf(w | x) over n vertices, with w drawn from the
     model's guide, or uniformly on the sphere (uniform=True, the "no guide"
-    baseline: the same kernel with uniform_frac = 1). fixed_position: the
-    guide sees that constant point (see online_step)."""
+    baseline: the same kernel with uniform_frac = 1). alpha > 0 draws from
+    the defensive one-sample mixture alpha uniform + (1 - alpha) guide (the
+    strategy the method samples with, Sec. 6.1), whose estimator is bounded
+    by target 4 pi / alpha. fixed_position: the guide sees that constant
+    point (see online_step)."""
     pos, aux, u = generate(seed, n, product, urows=4, stream=stream)
     d, p, _ = model.query_sample(_guide_input(pos, fixed_position), u, aux,
-                                 uniform_frac=1.0 if uniform else 0.0, stream=stream)
+                                 uniform_frac=1.0 if uniform else alpha, stream=stream)
     clean, _ = radiance(product, pos, aux, d, noisy=False, stream=stream)
     est = clean.double() / p.double()
     return float(est.var() / est.mean() ** 2), float(est.mean())
