@@ -336,15 +336,26 @@ npm_status npm_wavefront_run(npm_wavefront* w, int frames, void* stream, npm_fra
         rs = enqueue_frame(w, w->cap);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(w->cap, &g);
-        if (rs != NPM_OK) return rs;
+        if (rs != NPM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rs;
+        }
         if (e != cudaSuccess) return npm::set_error(NPM_ERR_CUDA, cudaGetErrorString(e));
         w->graph = g;
         if (cudaGraphInstantiate(&w->exec, g, 0) != cudaSuccess)
             return npm::set_error(NPM_ERR_CUDA, "cannot instantiate the frame graph");
     }
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    // Timing events, released on every return path.
+    struct Events {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        ~Events() {
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+        }
+    } ev;
+    if (cudaEventCreate(&ev.e0) != cudaSuccess || cudaEventCreate(&ev.e1) != cudaSuccess)
+        return npm::set_error(NPM_ERR_CUDA, "cannot create timing events");
+    const cudaEvent_t e0 = ev.e0, e1 = ev.e1;
     cudaEventRecord(e0, st);
     for (int f = 0; f < frames; ++f) {
         if (w->exec) {
@@ -357,8 +368,6 @@ npm_status npm_wavefront_run(npm_wavefront* w, int frames, void* stream, npm_fra
     if (cudaEventSynchronize(e1) != cudaSuccess) return npm::set_error(NPM_ERR_CUDA, "frames failed");
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     unsigned long long q1 = 0;
     cudaMemcpy(&q1, s.queries, 8, cudaMemcpyDeviceToHost);
     const int stride = s.bounces + 2;

@@ -327,8 +327,18 @@ npm_status npm_server_create(npm_handle* h, int64_t pool_queries, npm_server** o
         delete s;
         return npm::set_error(NPM_ERR_OOM, "cannot allocate the staging pool");
     }
-    for (int i = 0; i < 2; ++i) cudaStreamCreateWithFlags(&s->st[i], cudaStreamNonBlocking);
-    cudaEventCreateWithFlags(&s->last_train, cudaEventDisableTiming);
+    bool ok = true;
+    for (int i = 0; i < 2; ++i) ok = ok && cudaStreamCreateWithFlags(&s->st[i], cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&s->last_train, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        const char* msg = cudaGetErrorString(cudaGetLastError());
+        for (int i = 0; i < 2; ++i)
+            if (s->st[i]) cudaStreamDestroy(s->st[i]);
+        if (s->last_train) cudaEventDestroy(s->last_train);
+        cudaFree(s->pool);
+        delete s;
+        return npm::set_error(NPM_ERR_CUDA, msg);
+    }
     s->free_list[0] = pool_queries;
     s->worker = std::thread(worker_loop, s);
     *out = s;
