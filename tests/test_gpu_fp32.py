@@ -307,3 +307,29 @@ def test_query_sample_host_buffers_match_device(w, n, ld, alpha):
     assert np.array_equal(hd.numpy()[:, :n], host(d_dev)[:, :n])
     assert np.array_equal(hp.numpy()[:n], host(p_dev)[:n])
     assert np.all(hd.numpy()[:, n:] == -7.0) and np.all(hp.numpy()[n:] == -7.0)
+
+
+def test_readme_session():
+    # The usage shown in the README, at 2^16 vertices: densities of the
+    # library's own seeded initialisation match the oracle, and one training
+    # step on the sampled directions runs and moves the parameters.
+    import paper_2504_04315_gb300 as npm
+    w = synth.PAPER_HASH
+    n = 1 << 16
+    cfg = npm.make_config(npm.RADIANCE, level_res=w.level_res, feat=2, log2_table=19,
+                          widths=[32, 64, 64, 64, 32], K=8, precision=npm.FP32, max_batch=n)
+    m = npm.NPM(cfg)
+    p_init = m.get_params()
+    g = torch.Generator(device="cuda").manual_seed(0)
+    pos = torch.rand(3, n, device="cuda", generator=g)
+    u = torch.rand(3, n, device="cuda", generator=g)
+    d, pdf, _ = m.query_sample(pos, u)
+    k = 4096
+    ref = oracle.eval_pdf(w, p_init, host(pos)[:, :k], host(d)[:, :k], None)
+    assert rel_err(host(pdf)[:k], ref, 1e-30).max() < PDF_RTOL_FP32
+    radiance = torch.rand(n, device="cuda", generator=g)
+    loss = m.train_step(pos, d, radiance, pdf)
+    m.check_device_status()
+    assert math.isfinite(float(loss.item()))
+    assert not np.array_equal(m.get_params(), p_init)
+    m.close()
