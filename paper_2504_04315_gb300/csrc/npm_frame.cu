@@ -149,6 +149,9 @@ __global__ void k_wf_advance(WfState s, int b, int src) {
     const uint64_t ku = key(s.seed, f, b + 1, 2);
     const bool next = b + 1 < s.bounces;
     const unsigned lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
+    __shared__ int s_off[32];      // survivors per warp, then their offsets
+    __shared__ long long s_base;   // the block's first slot in the next queue
     for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = i0 + threadIdx.x;
         const bool valid = i < n;
@@ -175,13 +178,23 @@ __global__ void k_wf_advance(WfState s, int b, int src) {
                     x[r] = y - floorf(y);
                 }
         }
-        // Warp-aggregated compaction into the next queue.
+        // Block-aggregated compaction into the next queue: one atomic per
+        // block and pass, since atomics on one address serialise.
         const unsigned mask = __ballot_sync(0xffffffffu, keep);
-        int64_t base = 0;
-        if (lane == 0 && mask) base = (int64_t)atomicAdd((unsigned long long*)&s.count[dst], (unsigned long long)__popc(mask));
-        base = __shfl_sync(0xffffffffu, base, 0);
+        if (lane == 0) s_off[warp] = __popc(mask);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long tot = 0;
+            for (int w = 0; w < nwarps; ++w) {
+                const int c = s_off[w];
+                s_off[w] = (int)tot;
+                tot += (unsigned long long)c;
+            }
+            s_base = tot ? (long long)atomicAdd((unsigned long long*)&s.count[dst], tot) : 0ll;
+        }
+        __syncthreads();
         if (keep) {
-            const int64_t j = base + __popc(mask & ((1u << lane) - 1u));
+            const int64_t j = (int64_t)s_base + s_off[warp] + __popc(mask & ((1u << lane) - 1u));
             for (int r = 0; r < 3; ++r) s.pos[dst][r * s.P + j] = x[r];
             s.pid[dst][j] = p;
             if (next) write_uniforms(s, ku, j, (uint64_t)p);
