@@ -1,0 +1,41 @@
+"""The benchmark's roofline arithmetic on CPU: the algorithmic work per unit
+it divides by, and the bound it picks, against hand-computed values."""
+import os
+import sys
+
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+import bench  # noqa: E402
+import synth  # noqa: E402
+
+
+def test_mlp_flops_per_query():
+    # 2 * sum of layer products: 32-64-64-64-32 -> 24,576; 4-32-32-16 -> 3,328.
+    assert bench.mlp_flops(synth.PAPER_HASH) == 2 * (32 * 64 + 64 * 64 + 64 * 64 + 64 * 32) == 24576
+    assert bench.mlp_flops(synth.TINY_BF16) == 2 * (4 * 32 + 32 * 32 + 32 * 16) == 3328
+
+
+def test_tc_roofline_picks_the_smallest_bound():
+    pk = {"hbm_gbs": 8000.0, "bf16_tflops": 2000.0}
+    up = {"mufu_gops": 10000.0}
+    r = bench.tc_roofline(10e9, synth.TINY_BF16, pk, up, sms=152, sm_mhz=2000.0)
+    expect = {"hbm": 8000e9 / 40, "tensor": 2000e12 / 3328, "mufu": 10000e9 / 63,
+              "fp32_lanes": 152 * 128 * 2000e6 / 300}
+    for k, v in expect.items():
+        assert r["bounds"][k] == pytest.approx(v)
+    assert r["limiting_unit"] == "fp32_lanes" and r["bound"] == "alu"
+    assert r["frac"] == pytest.approx(10e9 / expect["fp32_lanes"])
+
+
+def test_train_roofline_adds_adam_and_scatter_time():
+    w = synth.PRODUCT_BF16
+    pk = {"hbm_gbs": 7000.0}
+    up = {"l2_atomic_v2_gops": 200.0}
+    n_params = 10_000_000
+    r = bench.train_roofline(5e8, w, n_params, pk, up)
+    step = 34.0 * n_params / 7000e9 + w.n_train * len(w.level_res) * 8 / 200e9
+    assert r["peak"] == pytest.approx(w.n_train / step)
+    assert r["frac"] == pytest.approx(5e8 * step / w.n_train)
+    assert r["atomics_per_sample"] == 128
