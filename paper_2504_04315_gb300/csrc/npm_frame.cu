@@ -50,11 +50,13 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
 }
 
 // Uniform in [0, 1) with 24 random bits: element i of the stream keyed by
-// s0 (the driver's counters stay below 2^32). Two 32-bit hash rounds cost a
-// fraction of a 64-bit mix per draw, and the driver draws eight per path and
-// bounce.
+// s0. Two 32-bit hash rounds cost a fraction of a 64-bit mix per draw, and
+// the driver draws eight per path and bounce. The high word of i (zero below
+// 2^32, i.e. below 2^30 paths) joins the key, so larger indices do not wrap
+// onto smaller ones.
 __device__ __forceinline__ float uni(uint64_t s0, uint64_t i) {
-    const uint32_t h = hash32(hash32((uint32_t)i + (uint32_t)s0) ^ (uint32_t)(s0 >> 32));
+    const uint32_t hi = (uint32_t)(s0 >> 32) ^ ((uint32_t)(i >> 32) * 0x9E3779B9u);
+    const uint32_t h = hash32(hash32((uint32_t)i + (uint32_t)s0) ^ hi);
     return (float)(h >> 8) * (1.0f / 16777216.0f);
 }
 
