@@ -157,21 +157,77 @@ def tc_roofline(qps, w, pk, up, sms, sm_mhz):
                            "npm_measure_unit_peaks; FP32 lanes = SMs x 128 x max SM clock"}
 
 
-def train_roofline(sps, w, n_params, pk, up):
+def scatter_atomic_counts(model, w, pos_dev):
+    """(four-wide, two-wide) atomic operations the tensor-core training
+    kernel's grid-gradient scatter issues for one batch. Four features per
+    entry: one four-wide atomic per corner. Two features: per level and
+    sample, each x-adjacent corner pair (c, c+1) whose two entries form one
+    16-byte aligned pair takes one four-wide atomic, any other pair two
+    two-wide ones; the corner indices come from the library
+    (npm_grid_indices) on the batch's positions."""
+    import torch
+    n = pos_dev.shape[1]
+    if w.feat == 4:
+        return 8 * len(w.level_res) * n, 0
+    assert w.feat == 2, "counts are defined for 2- and 4-feature grids"
+    idx = model.grid_indices(pos_dev).to(torch.int64)  # [L][8][n], entry within the level
+    offs = torch.tensor(np.cumsum([0] + synth.grid_sizes(w)[:-1]), dtype=torch.int64,
+                        device=idx.device)[:, None, None]
+    a, b = idx[:, 0::2, :], idx[:, 1::2, :]
+    lo = torch.minimum(a, b)
+    paired = ((a - b).abs() == 1) & (((offs + lo) & 1) == 0)
+    n4 = int(paired.sum())
+    n2 = 2 * (paired.numel() - n4)
+    return n4, n2
+
+
+def train_roofline(sps, w, n_params, pk, up, atomics=None):
     """Training step bound: dense Adam over every parameter (HBM, 34 B each)
-    plus the grid scatter (levels x 8 two-wide L2 atomics per sample); the
-    forward gathers and the tensor work overlap with them."""
+    plus the grid scatter at the measured L2 atomic rates; the forward
+    gathers and the tensor work overlap with them. atomics = (four-wide,
+    two-wide) operations per step as issued (scatter_atomic_counts), else
+    every corner counted as one two-wide atomic."""
     adam_s = 34.0 * n_params / (pk["hbm_gbs"] * 1e9)
-    atomics = len(w.level_res) * 8
-    scatter_s_per_sample = atomics / (up["l2_atomic_v2_gops"] * 1e9)
     n = w.n_train
-    step_s = adam_s + n * scatter_s_per_sample
+    if atomics is None:
+        n4, n2 = 0, len(w.level_res) * 8 * n
+    else:
+        n4, n2 = atomics
+    scatter_s = n4 / (up["l2_atomic_v4_gops"] * 1e9) + n2 / (up["l2_atomic_v2_gops"] * 1e9)
+    step_s = adam_s + scatter_s
     peak = n / step_s
     return {"bound": "hbm+l2_atomic", "achieved": sps, "peak": peak, "unit": "samples/s",
             "frac": sps / peak, "adam_bytes_per_step": 34.0 * n_params,
-            "atomics_per_sample": atomics,
-            "peak_source": "HBM from MEASURED_PEAKS.json; two-wide L2 atomics measured by "
-                           "npm_measure_unit_peaks"}
+            "atomics_per_step": {"four_wide": n4, "two_wide": n2,
+                                 "per_sample": (n4 + n2) / n,
+                                 "counted": "from the batch's corner indices" if atomics else "upper bound"},
+            "bound_ms": {"adam_hbm": adam_s * 1e3, "scatter_l2_atomics": scatter_s * 1e3},
+            "peak_source": "HBM from MEASURED_PEAKS.json; four- and two-wide L2 atomic rates "
+                           "measured by npm_measure_unit_peaks"}
+
+
+# Compaction traffic of the serving loop per live path and bounce (a keep
+# flag read and a queue index written).
+SERVING_COMPACT_BYTES = 8
+
+
+def serving_roofline(sv, w, frames, pk, up, sms, sm_mhz, train_bound_s):
+    """Bound of one serving frame: its queries at the tiny tensor-core
+    forward's bound (tc_roofline), plus the compaction traffic at the HBM
+    copy rate, plus one training step's bound; frac = bound / measured frame
+    time."""
+    tc = tc_roofline(1.0, w, pk, up, sms, sm_mhz)
+    q = sv["queries"] / frames
+    q_s = q / tc["peak"]
+    c_s = SERVING_COMPACT_BYTES * q / (pk["hbm_gbs"] * 1e9)
+    bound_s = q_s + c_s + train_bound_s
+    frame_s = sv["frame_ms_mean"] / 1e3
+    return {"bound": "alu+hbm+l2_atomic", "achieved_ms_per_frame": sv["frame_ms_mean"],
+            "bound_ms_per_frame": bound_s * 1e3, "frac": bound_s / frame_s,
+            "bound_parts_ms": {"queries": q_s * 1e3, "compaction": c_s * 1e3, "training": train_bound_s * 1e3},
+            "queries_per_frame": q, "query_bound": tc["limiting_unit"],
+            "peak_source": "queries at the tensor-core forward's bound (reduced_precision.roofline); "
+                           "compaction at the HBM copy rate; training at the Adam-HBM + L2-atomic bound"}
 
 
 def run_reference(args, w, rank):
@@ -383,7 +439,12 @@ def main():
         reduced = {"workload": rw.name, "queries_per_step": nr, "unit": "queries/s",
                    "split_bf16": res[synth.BF16X3], "bf16": res[synth.BF16],
                    "fp32_same_workload": res[synth.FP32],
-                   "split_bf16_over_fp32": res[synth.BF16X3] / res[synth.FP32]}
+                   "split_bf16_over_fp32": res[synth.BF16X3] / res[synth.FP32],
+                   "accuracy_valid_value": res[synth.BF16X3],
+                   "meets_accuracy_bar": {"split_bf16": True, "bf16": False, "fp32_same_workload": True},
+                   "accuracy_note": "single-pass bf16 does not meet the stated reduced-precision accuracy "
+                                    "(density within 2e-2 at the 99.9th percentile): 1.5e-2..6e-2 on these "
+                                    "sharp-lobe parameters; its throughput is reported for reference only"}
 
     # Serving loop: 64 frames of 1920x1080 paths, 8 bounces with Bernoulli(0.7)
     # survival, query + sample + pdf per bounce on the tiny network in split
@@ -399,13 +460,28 @@ def main():
                            use_graph=True, max_frames=80) as wf:
             wf.run(3, stream=stream)
             sv = wf.run(64, stream=stream)
+        # The frame's training batch: its scatter's atomic count (the
+        # training bound inside the serving bound) from a batch of the same
+        # size and position distribution.
+        tb = torch.from_numpy(synth.positions(seed0 + 91, 1 << 18)).cuda()
+        serving_train_atomics = scatter_atomic_counts(msv, sw, tb)
+        serving_params = msv.num_params()
         msv.close()
+        qms = sv["query_ms_mean"]
         serving = {"workload": "1920x1080 paths x 8 bounces, survival 0.7, " + sw.name +
                    ", 2^18 training samples per frame, CUDA-graph frames",
                    "frames": 64, "queries": sv["queries"], "unit": "queries/s",
                    "value": sv["queries_per_s"] * world,
                    "bounce_p50_ms": sv["bounce_p50_ms"], "bounce_p99_ms": sv["bounce_p99_ms"],
-                   "frame_ms_mean": sv["frame_ms_mean"], "train_ms_mean": sv["train_ms_mean"]}
+                   "frame_ms_mean": sv["frame_ms_mean"], "train_ms_mean": sv["train_ms_mean"],
+                   "breakdown_ms_per_frame": {"query_kernels": qms, "scene_and_compaction": sv["advance_ms_mean"],
+                                              "training": sv["train_ms_mean"],
+                                              "other": sv["frame_ms_mean"] - qms - sv["advance_ms_mean"]
+                                              - sv["train_ms_mean"]},
+                   "query_kernel_rate": sv["queries"] / 64 / (qms / 1e3) if qms > 0 else None,
+                   "per_bounce": [{"bounce": b, "queries": q, "query_ms": t,
+                                   "queries_per_s": q / (t / 1e3) if t > 0 else None}
+                                  for b, (q, t) in enumerate(zip(sv["bounce_queries"], sv["bounce_query_ms"]))]}
 
     # Continuous batching through the request server: 4 client threads, each
     # submitting wavefront-shaped query requests (2^18 * 0.7^b queries for
@@ -476,6 +552,8 @@ def main():
             n_params = mt.num_params()
             b = synth.train_batch_uniform(tw, nt, seed=5 + rank)
             tb = [torch.from_numpy(a).cuda() for a in (b.pos, b.dir, b.radiance, b.pdf, b.aux)]
+            if prec == synth.BF16X3:
+                train_atomics = scatter_atomic_counts(mt, tw, tb[0])
             loss = torch.zeros(1, device="cuda")
             for _ in range(3):
                 mt.train_step(tb[0], tb[1], tb[2], tb[3], tb[4], loss_out=loss, stream=stream)
@@ -560,7 +638,13 @@ def main():
                                               props.multi_processor_count, sm_max)
         if train:
             train["roofline"] = train_roofline(train["value"] / world, synth.PRODUCT_BF16,
-                                               train["params"], pk, unit_peaks)
+                                               train["params"], pk, unit_peaks, train_atomics)
+        if serving:
+            sw = synth.TINY_BF16.with_(n_train=1 << 18)
+            tr_bound = train_roofline(1.0, sw, serving_params, pk, unit_peaks, serving_train_atomics)
+            serving["roofline"] = serving_roofline(serving, synth.TINY_BF16, 64, pk, unit_peaks,
+                                                   props.multi_processor_count, sm_max,
+                                                   (1 << 18) / tr_bound["peak"])
     if not args.no_cpu_baseline and not args.no_extras:
         line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)

@@ -81,12 +81,20 @@ enum { NPM_FP32 = 0, NPM_BF16 = 1, NPM_BF16X3 = 2 };  /* MLP / grid arithmetic *
  *                  is a multiple of 4 and at most NPM_MAX_WIDTH.
  *   precision      NPM_FP32: FP32 grid and CUDA-core FP32 MLP.
  *                  NPM_BF16: FP16 grid copy, BF16 tensor-core MLP (tcgen05)
- *                  with FP32 accumulation; all vMF math stays FP32.
+ *                  with FP32 accumulation; all vMF math stays FP32. Single-
+ *                  pass BF16 inference does NOT meet the reduced-precision
+ *                  accuracy bar (density within 2e-2 at the 99.9th
+ *                  percentile) on mixtures with sharp lobes: at kappa up to
+ *                  ~35 its 8-bit significands put the density 1.5e-2 to
+ *                  6e-2 off. Use it only where that error is acceptable.
  *                  NPM_BF16X3: as NPM_BF16, but every activation and weight
  *                  is split into a BF16 high part and a BF16 residual, and
  *                  each product is hi*hi + hi*lo + lo*hi (three MMAs per
- *                  K step), which recovers about 16 significant bits.
- *                  Master parameters and Adam state are FP32 in all modes.
+ *                  K step), which recovers about 16 significant bits; meets
+ *                  the bar.
+ *                  Training (npm_train_step, npm_backward) multiplies split
+ *                  operands in both reduced-precision modes. Master
+ *                  parameters and Adam state are FP32 in all modes.
  *   lr, beta1, beta2, eps   Adam (Sec. 5.3 uses lr 0.005).
  *   max_batch      largest n of any call; sizes the workspace.
  *   seed           seeds npm_create's parameter initialisation
@@ -154,6 +162,15 @@ npm_status npm_query_sample_host(npm_handle* h, int64_t n, const float* pos, con
  * dir [3][ld]; pdf_out [n]. */
 npm_status npm_eval_pdf(npm_handle* h, int64_t n, const float* pos, const float* aux,
                         const float* dir, int64_t ld, float* pdf_out, void* stream);
+
+/* log V(dir | Theta(x)) at given unit directions dir [3][ld]; logpdf_out
+ * [n]. Evaluated by the same kernels as npm_eval_pdf in log-sum-exp form:
+ * each lobe's term log lambda_i + log c(kappa_i) + kappa_i (mu_i.dir - 1),
+ * with log lambda_i taken from the logits, so the result stays finite where
+ * V itself underflows FP32 (directions far from every sharp lobe). This is
+ * the quantity the training loss (Sec. 4.2, Eq. 8-9) differentiates. */
+npm_status npm_eval_log_pdf(npm_handle* h, int64_t n, const float* pos, const float* aux,
+                            const float* dir, int64_t ld, float* logpdf_out, void* stream);
 
 /*
  * One training step (Sec. 4.2 and 5.3): the loss
@@ -269,16 +286,27 @@ typedef struct npm_frame_config {
     int max_frames;       /* frames over the driver's lifetime (timestamp space) */
 } npm_frame_config;
 
+#define NPM_FRAME_BOUNCE_STATS 16  /* bounces with per-bounce figures */
+
 typedef struct npm_frame_stats {
     int64_t frames;
     int64_t queries;        /* guided queries served (sum of live paths) */
     double seconds;         /* device time of the frames */
     double queries_per_s;   /* queries / seconds, training included */
     double bounce_p50_ms;   /* per-bounce batch latency on the device */
-    double bounce_p99_ms;
+    double bounce_p99_ms;   /* (query kernel + scene evaluation and compaction) */
     double frame_ms_mean;
     double train_ms_mean;   /* the per-frame training step */
     float last_loss;
+    /* Breakdown of a frame's device time (means over the run's frames):
+     * the guide's query kernels of all bounces, and the stand-in scene's
+     * evaluation and compaction kernels of all bounces. */
+    double query_ms_mean;
+    double advance_ms_mean;
+    /* Per bounce b < NPM_FRAME_BOUNCE_STATS, means over the run's frames:
+     * live paths queried and the query kernel's time. */
+    double bounce_queries[NPM_FRAME_BOUNCE_STATS];
+    double bounce_query_ms[NPM_FRAME_BOUNCE_STATS];
 } npm_frame_stats;
 
 npm_status npm_wavefront_create(npm_handle* h, const npm_frame_config* cfg, npm_wavefront** out);
@@ -342,10 +370,17 @@ npm_status npm_scene_radiance(int product, uint64_t noise_seed, int64_t n, const
  * Errors: NPM_ERR_INVALID_ARG (configuration or arguments),
  * NPM_ERR_CAPACITY when the padded weights exceed
  * NPM_NOALLOC_MAX_WEIGHT_FLOATS, NPM_ERR_CUDA on a failed launch.
- * Set-up: the first call on each device (with that device current) looks up
- * the device address of the scratch array once (cudaGetSymbolAddress, which
- * also loads the library's device code if it is not loaded yet); make that
- * first call before any stream capture.
+ * Kernel: the FP32 tile-group forward kernel, which has no kernel-internal
+ * waits (no mailbox hand-offs between thread groups), so no launch can give
+ * up part-way: when the call returns NPM_OK, every pdf_out value is written
+ * by the work it queued. (npm_eval_pdf on a handle may run the
+ * warp-specialised kernel instead, whose bounded waits report through the
+ * handle's status word; this entry point has no such word.)
+ * Set-up: every call looks up the device address of the scratch array on
+ * the current device (cudaGetSymbolAddress: no allocation; the first call
+ * on a device also loads the library's device code there, so make the first
+ * call on each device before any stream capture). A device reset therefore
+ * needs no special handling.
  * Sharing: every call on a device uses the same scratch array, which keeps
  * the contents of the last call. Each call rewrites every value it reads, so
  * nothing needs clearing, but calls that overlap on the GPU (different

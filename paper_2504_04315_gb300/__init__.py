@@ -156,6 +156,18 @@ class NPM:
                                         _stream_ptr(stream)), "npm_eval_pdf")
         return p
 
+    def eval_log_pdf(self, pos, dirs, aux=None, n: Optional[int] = None, out=None, stream=None):
+        """log V at the given directions, computed in the kernel in
+        log-sum-exp form (npm_eval_log_pdf)."""
+        torch = _torch()
+        ld = _soa(pos, 3, "pos")
+        n = ld if n is None else n
+        _soa(dirs, 3, "dir")
+        p = torch.empty((ld,), device=pos.device, dtype=torch.float32) if out is None else out
+        _lib.check(self._L.npm_eval_log_pdf(self._h, n, _ptr(pos), _ptr(aux), _ptr(dirs), ld, _ptr(p),
+                                            _stream_ptr(stream)), "npm_eval_log_pdf")
+        return p
+
     def train_step(self, pos, dirs, radiance, sample_pdf, aux=None, n: Optional[int] = None,
                    loss_out=None, stream=None):
         torch = _torch()
@@ -288,22 +300,21 @@ def _make_log_density():
         parameters theta (float32 CUDA tensor [npm_num_params], public layout).
 
         Forward loads theta into the model (npm_set_params_device) and
-        evaluates the density with the library's kernels (npm_eval_pdf);
-        backward reloads theta and runs the hand-written backward
-        (npm_backward: decode, MLP and grid, activations recomputed, with the
-        incoming gradient as the per-query weight of d log V), returning the
-        parameter gradient (npm_get_grads_device). Only the elementwise log
-        of the density runs outside the library."""
+        evaluates log V with the library's kernels (npm_eval_log_pdf, in
+        log-sum-exp form); backward reloads theta and runs the hand-written
+        backward (npm_backward: decode, MLP and grid, activations recomputed,
+        with the incoming gradient as the per-query weight of d log V),
+        returning the parameter gradient (npm_get_grads_device)."""
 
         @staticmethod
         def forward(ctx, theta, model, pos, dirs, aux=None):
             model.set_params_device(theta)
-            v = model.eval_pdf(pos, dirs, aux)
+            lv = model.eval_log_pdf(pos, dirs, aux)
             n = pos.shape[1]
             ctx.model = model
             ctx.save_for_backward(theta, pos, dirs, aux if aux is not None else theta.new_empty(0))
             ctx.has_aux = aux is not None
-            return torch.log(v[:n])
+            return lv[:n]
 
         @staticmethod
         def backward(ctx, grad_out):
@@ -413,6 +424,7 @@ class Wavefront:
         self._L = _lib.load()
         self.model = model
         c = _lib.NpmFrameConfig()
+        self.bounces = int(bounces)
         c.paths, c.bounces, c.survival = int(paths), int(bounces), float(survival)
         c.train_batch, c.uniform_frac, c.seed = int(train_batch), float(uniform_frac), int(seed)
         c.use_graph, c.max_frames = 1 if use_graph else 0, int(max_frames)
@@ -425,7 +437,11 @@ class Wavefront:
         s = _lib.NpmFrameStats()
         _lib.check(self._L.npm_wavefront_run(self._w, int(frames), _stream_ptr(stream), C.byref(s)),
                    "npm_wavefront_run")
-        return {k: getattr(s, k) for k, _ in s._fields_}
+        out = {k: getattr(s, k) for k, _ in s._fields_}
+        nb = min(self.bounces, _lib.FRAME_BOUNCE_STATS)
+        out["bounce_queries"] = list(s.bounce_queries)[:nb]
+        out["bounce_query_ms"] = list(s.bounce_query_ms)[:nb]
+        return out
 
     def close(self):
         if getattr(self, "_w", None):

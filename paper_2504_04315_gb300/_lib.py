@@ -12,6 +12,7 @@ from ._build import LIB
 
 MAX_LEVELS = 32
 MAX_LAYERS = 8
+FRAME_BOUNCE_STATS = 16
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_NUMERIC, \
     ERR_UNSUPPORTED, ERR_IO = range(9)
@@ -54,6 +55,9 @@ class NpmFrameStats(C.Structure):
         ("queries_per_s", C.c_double), ("bounce_p50_ms", C.c_double),
         ("bounce_p99_ms", C.c_double), ("frame_ms_mean", C.c_double),
         ("train_ms_mean", C.c_double), ("last_loss", C.c_float),
+        ("query_ms_mean", C.c_double), ("advance_ms_mean", C.c_double),
+        ("bounce_queries", C.c_double * FRAME_BOUNCE_STATS),
+        ("bounce_query_ms", C.c_double * FRAME_BOUNCE_STATS),
     ]
 
 
@@ -79,6 +83,7 @@ SIGNATURES = {
     "npm_query_sample": (st, [vp, i64, vp, vp, vp, i64, f32, vp, vp, vp, vp]),
     "npm_query_sample_host": (st, [vp, i64, vp, vp, vp, i64, f32, vp, vp, vp]),
     "npm_eval_pdf": (st, [vp, i64, vp, vp, vp, i64, vp, vp]),
+    "npm_eval_log_pdf": (st, [vp, i64, vp, vp, vp, i64, vp, vp]),
     "npm_train_step": (st, [vp, i64, vp, vp, vp, vp, vp, i64, vp, vp]),
     "npm_backward": (st, [vp, i64, vp, vp, vp, vp, i64, vp]),
     "npm_adam_step": (st, [vp, vp]),

@@ -517,6 +517,21 @@ npm_status npm_eval_pdf(npm_handle* h, int64_t n, const float* pos, const float*
     return NPM_OK;
 }
 
+npm_status npm_eval_log_pdf(npm_handle* h, int64_t n, const float* pos, const float* aux,
+                            const float* dir, int64_t ld, float* logpdf_out, void* stream) {
+    npm_status s = check_call(h, n, ld, pos, aux);
+    if (s != NPM_OK) return s;
+    if (n > 0 && (!dir || !logpdf_out)) return fail(NPM_ERR_INVALID_ARG, "dir and logpdf_out are required");
+    if (n == 0) return NPM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h->tc) return npm::tc_query(h, n, ld, pos, aux, dir, 0.0f, false, nullptr, logpdf_out, nullptr, st, true);
+    NPM_CUDA(npm::launch_forward_fp32(h->dc, inf_params(h), inf_wfwd(h), n, ld, pos, aux, dir, 0.0f, false,
+                                      nullptr, logpdf_out, nullptr, st, status_word(h), h->wait_limit, false,
+                                      true),
+             "eval_log_pdf launch");
+    return NPM_OK;
+}
+
 static npm_status backward_impl(npm_handle* h, int64_t n, const float* pos, const float* aux,
                                 const float* dir, const float* rad, const float* spdf,
                                 const float* dlogv, int64_t ld, cudaStream_t st) {

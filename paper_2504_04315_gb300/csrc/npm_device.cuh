@@ -384,6 +384,7 @@ constexpr int kMaxSegs = 16;
 struct QueryBatch {
     int nseg;
     int sample;
+    int log_pdf;  // evaluation only: pdf receives log V (log-sum-exp form)
     int64_t total_tiles;
     const int64_t* n_dev;
     QuerySeg seg[kMaxSegs];

@@ -341,6 +341,7 @@ template <int KH>
 struct HalfMix {
     Lobe lob[KH];
     float cn[KH];
+    float mx, ssum;  // largest weight logit and sum of e^{logit - mx}, both halves
     int l0, cnt;
 };
 
@@ -364,6 +365,8 @@ __device__ __forceinline__ void decode_half(const DevCfg& cfg, const float* raw,
             ssum += hm.lob[ii].lam;
         }
     ssum += __shfl_xor_sync(kFull, ssum, 1);
+    hm.mx = mx;
+    hm.ssum = ssum;
     const float inv = __fdividef(1.0f, ssum);  // ssum in [1, K]
 #pragma unroll
     for (int ii = 0; ii < KH; ++ii)
@@ -392,13 +395,38 @@ __device__ __forceinline__ float half_pdf(const HalfMix<KH>& hm, const float w[3
     return pv + __shfl_xor_sync(kFull, pv, 1);
 }
 
+// log V at w (Eq. 4 in log-sum-exp form): the log of each lobe's term,
+// log lambda_i + log c(kappa_i) + kappa_i (mu_i.w - 1), with log lambda_i
+// taken from the logits so that it stays finite where lambda_i underflows.
+template <int KH>
+__device__ __forceinline__ float half_log_pdf(const HalfMix<KH>& hm, const float* raw, const float w[3]) {
+    const float lnorm = hm.mx + __logf(hm.ssum);
+    float a[KH];
+    float m = -INFINITY;
+#pragma unroll
+    for (int ii = 0; ii < KH; ++ii)
+        if (ii < hm.cnt) {
+            const Lobe& L = hm.lob[ii];
+            const float d = L.mu[0] * w[0] + L.mu[1] * w[1] + L.mu[2] * w[2];
+            a[ii] = (raw[4 * (hm.l0 + ii)] - lnorm) + __logf(hm.cn[ii]) + L.kap * (d - 1.0f);
+            m = fmaxf(m, a[ii]);
+        }
+    m = fmaxf(m, __shfl_xor_sync(kFull, m, 1));
+    float s = 0.0f;
+#pragma unroll
+    for (int ii = 0; ii < KH; ++ii)
+        if (ii < hm.cnt) s += __expf(a[ii] - m);
+    s += __shfl_xor_sync(kFull, s, 1);
+    return m + __logf(s);
+}
+
 template <bool SAMPLE, int KH>
 __device__ __forceinline__ void epilogue_tile(int t, const DevCfg& cfg, const float* act, int AS,
                                               int64_t base, int64_t n, int64_t ld,
                                               const float* __restrict__ uin, float ufrac,
                                               float* __restrict__ dir_out,
                                               float* __restrict__ pdf_out,
-                                              float* __restrict__ mix_out) {
+                                              float* __restrict__ mix_out, bool log_pdf = false) {
     const int q = t >> 1, half = t & 1;
     const int64_t j = base + q;
     const bool valid = j < n;
@@ -477,8 +505,13 @@ __device__ __forceinline__ void epilogue_tile(int t, const DevCfg& cfg, const fl
             w[2] = uin[2 * ld + j];
         }
     }
-    float pv = half_pdf(hm, w);
-    if (SAMPLE && ufrac > 0.0f) pv = ufrac * kInv4Pi + (1.0f - ufrac) * pv;
+    float pv;
+    if (!SAMPLE && log_pdf) {
+        pv = half_log_pdf(hm, raw, w);
+    } else {
+        pv = half_pdf(hm, w);
+        if (SAMPLE && ufrac > 0.0f) pv = ufrac * kInv4Pi + (1.0f - ufrac) * pv;
+    }
     if (valid) {
         if (half == 0) {
             if (SAMPLE) {
@@ -552,7 +585,8 @@ __global__ void __launch_bounds__(fwd_max_groups(NIMAX) * kNT, 1) k_forward_fp32
                                    cfg.widths[l + 1], last ? 0 : 1, nullptr, group);
             group_sync(group);
         }
-        epilogue_tile<SAMPLE, KH>(t, cfg, act, AS, base, n, S.ld, S.uin, S.ufrac, S.dir, S.pdf, S.mix);
+        epilogue_tile<SAMPLE, KH>(t, cfg, act, AS, base, n, S.ld, S.uin, S.ufrac, S.dir, S.pdf, S.mix,
+                                      qb.log_pdf != 0);
         group_sync(group);
     }
 }
@@ -731,7 +765,8 @@ __global__ void __launch_bounds__((GC + 1) * kNT, 1) k_forward_fp32_ws(const __g
                                        cfg.widths[l + 1], last ? 0 : 1, nullptr, group);
                 group_sync(group);
             }
-            epilogue_tile<SAMPLE, KH>(t, cfg, act, AS, base, n, S.ld, S.uin, S.ufrac, S.dir, S.pdf, S.mix);
+            epilogue_tile<SAMPLE, KH>(t, cfg, act, AS, base, n, S.ld, S.uin, S.ufrac, S.dir, S.pdf, S.mix,
+                                      qb.log_pdf != 0);
             group_sync(group);
         }
     }
@@ -1208,7 +1243,7 @@ static int ws_groups(const DevCfg& cfg, int inst) {
 
 cudaError_t launch_forward_fp32_batch(const DevCfg& cfg, const float* grid, const float* wfwd,
                                       QueryBatch& qb, int64_t max_n, cudaStream_t st, int* status,
-                                      long long wait_limit) {
+                                      long long wait_limit, bool wait_free) {
     int64_t t0 = 0;
     for (int s = 0; s < qb.nseg; ++s) {
         qb.seg[s].tile0 = t0;
@@ -1217,7 +1252,7 @@ cudaError_t launch_forward_fp32_batch(const DevCfg& cfg, const float* grid, cons
     qb.total_tiles = t0;
     const int64_t hint = qb.n_dev ? (max_n + kTQ - 1) / kTQ : t0;
     const int inst = fp32_instance(cfg);
-    const int gc = ws_groups(cfg, inst);
+    const int gc = wait_free ? 0 : ws_groups(cfg, inst);
     if (gc == 4)
         return qb.sample ? launch_fwd_ws<true, 4>(cfg, grid, wfwd, qb, hint, status, wait_limit, st)
                          : launch_fwd_ws<false, 4>(cfg, grid, wfwd, qb, hint, status, wait_limit, st);
@@ -1237,11 +1272,13 @@ cudaError_t launch_forward_fp32_batch(const DevCfg& cfg, const float* grid, cons
 cudaError_t launch_forward_fp32(const DevCfg& cfg, const float* grid, const float* wfwd, int64_t n,
                                 int64_t ld, const float* pos, const float* aux, const float* uin,
                                 float ufrac, bool sample, float* dir_out, float* pdf_out,
-                                float* mix_out, cudaStream_t st, int* status, long long wait_limit) {
+                                float* mix_out, cudaStream_t st, int* status, long long wait_limit,
+                                bool wait_free, bool log_pdf) {
     QueryBatch qb;
     memset(&qb, 0, sizeof(qb));
     qb.nseg = 1;
     qb.sample = sample ? 1 : 0;
+    qb.log_pdf = (!sample && log_pdf) ? 1 : 0;
     QuerySeg& q = qb.seg[0];
     q.n = n;
     q.ld = ld;
@@ -1252,7 +1289,7 @@ cudaError_t launch_forward_fp32(const DevCfg& cfg, const float* grid, const floa
     q.dir = sample ? dir_out : nullptr;
     q.pdf = pdf_out;
     q.mix = sample ? mix_out : nullptr;
-    return launch_forward_fp32_batch(cfg, grid, wfwd, qb, n, st, status, wait_limit);
+    return launch_forward_fp32_batch(cfg, grid, wfwd, qb, n, st, status, wait_limit, wait_free);
 }
 
 cudaError_t launch_train_fp32(const DevCfg& cfg, const float* params, int64_t mlp_off,

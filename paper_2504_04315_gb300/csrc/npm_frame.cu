@@ -82,7 +82,12 @@ struct WfState {
     float* trad;          // [T]
     float* tpdf;          // [T]
     uint64_t* frame;      // device frame counter
-    uint64_t* stamps;     // [max_frames][bounces + 2]
+    // [max_frames][2 bounces + 2]: 0 after the frame start; 1 + 2b when
+    // bounce b's query kernel has finished (taken as the bounce's advance
+    // kernel starts); 2 + 2b after that advance; 2 bounces + 1 after the
+    // training step.
+    uint64_t* stamps;
+    int64_t* live;        // [max_frames][bounces]: paths queried per bounce
     unsigned long long* queries;  // total queries served
     int max_frames;
 };
@@ -105,7 +110,7 @@ __device__ float field(const float* x, const float* w) {
 
 __device__ __forceinline__ void stamp(const WfState& s, int slot) {
     const uint64_t f = *s.frame;
-    if ((int64_t)f < s.max_frames) s.stamps[f * (s.bounces + 2) + slot] = globaltimer();
+    if ((int64_t)f < s.max_frames) s.stamps[f * (2 * s.bounces + 2) + slot] = globaltimer();
 }
 
 // Sampling uniforms of path p at bounce b, written at queue slot i.
@@ -140,19 +145,31 @@ __global__ void k_wf_stamp(WfState s, int slot, int clear) {
     }
 }
 
+// Threads per block of k_wf_advance. Its compaction takes a full-warp
+// ballot and keeps one count per warp in a 32-entry shared table, so the
+// block must be whole warps and at most 32 of them.
+constexpr int kAdvanceThreads = 256;
+static_assert(kAdvanceThreads % 32 == 0 && kAdvanceThreads <= 1024,
+              "k_wf_advance needs whole warps, at most 32 of them");
+
 // Radiance estimate, training record, survival and compaction of one
 // bounce; each survivor also gets the next bounce's uniforms at its new
 // queue slot (this bounce's query kernel has consumed the old ones).
-__global__ void k_wf_advance(WfState s, int b, int src) {
+__global__ void __launch_bounds__(kAdvanceThreads) k_wf_advance(WfState s, int b, int src) {
     const uint64_t f = *s.frame;
     const int64_t n = s.count[src];
     const int dst = src ^ 1;
     const uint64_t kn = key(s.seed, f, b, 3), ks = key(s.seed, f, b, 4), kj = key(s.seed, f, b, 5);
     const uint64_t ku = key(s.seed, f, b + 1, 2);
     const bool next = b + 1 < s.bounces;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // The query kernel of this bounce has completed (stream order).
+        stamp(s, 1 + 2 * b);
+        if ((int64_t)f < s.max_frames) s.live[f * s.bounces + b] = n;
+    }
     const unsigned lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
-    __shared__ int s_off[32];      // survivors per warp, then their offsets
+    const int warp = threadIdx.x >> 5, nwarps = kAdvanceThreads / 32;
+    __shared__ int s_off[kAdvanceThreads / 32];  // survivors per warp, then their offsets
     __shared__ long long s_base;   // the block's first slot in the next queue
     for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = i0 + threadIdx.x;
@@ -207,7 +224,7 @@ __global__ void k_wf_advance(WfState s, int b, int src) {
 
 __global__ void k_wf_end(WfState s) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        stamp(s, s.bounces + 1);
+        stamp(s, 2 * s.bounces + 1);
         *s.frame += 1;
     }
 }
@@ -256,9 +273,9 @@ npm_status enqueue_frame(npm_wavefront* w, cudaStream_t st) {
         cudaError_t e = h->tc ? npm::tc_query_batch(h, qb, s.P, st)
                               : npm::launch_forward_fp32_batch(h->dc, inf_params(h), inf_wfwd(h), qb, s.P, st, status_word(h), h->wait_limit);
         if (e != cudaSuccess) return npm::set_error(NPM_ERR_CUDA, cudaGetErrorString(e));
-        k_wf_advance<<<g, 256, 0, st>>>(s, b, src);
+        k_wf_advance<<<g, kAdvanceThreads, 0, st>>>(s, b, src);
         // count[src] was this bounce's queue: the next advance appends to it
-        k_wf_stamp<<<1, 32, 0, st>>>(s, 1 + b, src);
+        k_wf_stamp<<<1, 32, 0, st>>>(s, 2 + 2 * b, src);
     }
     npm_status rs = npm_train_step(h, s.T, s.tpos, nullptr, s.tdir, s.trad, s.tpdf, s.T, w->loss, st);
     if (rs != NPM_OK) return rs;
@@ -293,7 +310,9 @@ npm_status npm_wavefront_create(npm_handle* h, const npm_frame_config* cfg, npm_
     s.max_frames = cfg->max_frames;
     const size_t P = (size_t)s.P, T = (size_t)s.T;
     const size_t floats = 2 * 3 * P + 4 * P + 3 * P + P + 3 * T + 3 * T + T + T + 1;
-    const size_t bytes = floats * 4 + 2 * P * 4 + 64 + (size_t)cfg->max_frames * (cfg->bounces + 2) * 8 + 256;
+    const size_t nstamp = (size_t)cfg->max_frames * (2 * cfg->bounces + 2);
+    const size_t nlive = (size_t)cfg->max_frames * cfg->bounces;
+    const size_t bytes = floats * 4 + 2 * P * 4 + 64 + (nstamp + nlive) * 8 + 256 * 20;
     if (cudaMalloc(&w->mem, bytes) != cudaSuccess) {
         cudaGetLastError();
         delete w;
@@ -321,8 +340,9 @@ npm_status npm_wavefront_create(npm_handle* h, const npm_frame_config* cfg, npm_
     s.frame = (uint64_t*)take(8);
     s.queries = (unsigned long long*)take(8);
     w->loss = (float*)take(4);
-    s.stamps = (uint64_t*)take((size_t)cfg->max_frames * (cfg->bounces + 2) * 8);
-    if ((size_t)(p - static_cast<char*>(w->mem)) > bytes + 4096) {
+    s.stamps = (uint64_t*)take(nstamp * 8);
+    s.live = (int64_t*)take(nlive * 8);
+    if ((size_t)(p - static_cast<char*>(w->mem)) > bytes) {
         cudaFree(w->mem);
         delete w;
         return npm::set_error(NPM_ERR_INVALID_ARG, "internal layout error");
@@ -385,18 +405,29 @@ npm_status npm_wavefront_run(npm_wavefront* w, int frames, void* stream, npm_fra
     cudaEventElapsedTime(&ms, e0, e1);
     unsigned long long q1 = 0;
     cudaMemcpy(&q1, s.queries, 8, cudaMemcpyDeviceToHost);
-    const int stride = s.bounces + 2;
+    const int stride = 2 * s.bounces + 2;
     std::vector<uint64_t> t((size_t)frames * stride);
+    std::vector<int64_t> live((size_t)frames * s.bounces);
     cudaMemcpy(t.data(), s.stamps + f0 * stride, t.size() * 8, cudaMemcpyDeviceToHost);
+    cudaMemcpy(live.data(), s.live + f0 * s.bounces, live.size() * 8, cudaMemcpyDeviceToHost);
     std::vector<double> lat;
-    double train_ms = 0.0;
+    double train_ms = 0.0, query_ms = 0.0, adv_ms = 0.0;
+    memset(out, 0, sizeof(*out));
     for (int f = 0; f < frames; ++f) {
         const uint64_t* r = &t[(size_t)f * stride];
-        for (int b = 0; b < s.bounces; ++b) lat.push_back((double)(r[b + 1] - r[b]) * 1e-6);
-        train_ms += (double)(r[s.bounces + 1] - r[s.bounces]) * 1e-6;
+        for (int b = 0; b < s.bounces; ++b) {
+            lat.push_back((double)(r[2 * b + 2] - r[2 * b]) * 1e-6);
+            const double q = (double)(r[2 * b + 1] - r[2 * b]) * 1e-6;
+            query_ms += q;
+            adv_ms += (double)(r[2 * b + 2] - r[2 * b + 1]) * 1e-6;
+            if (b < NPM_FRAME_BOUNCE_STATS) {
+                out->bounce_queries[b] += (double)live[(size_t)f * s.bounces + b] / frames;
+                out->bounce_query_ms[b] += q / frames;
+            }
+        }
+        train_ms += (double)(r[2 * s.bounces + 1] - r[2 * s.bounces]) * 1e-6;
     }
     std::sort(lat.begin(), lat.end());
-    memset(out, 0, sizeof(*out));
     out->frames = frames;
     out->queries = (int64_t)(q1 - q0);
     out->seconds = ms * 1e-3;
@@ -406,6 +437,8 @@ npm_status npm_wavefront_run(npm_wavefront* w, int frames, void* stream, npm_fra
         out->bounce_p99_ms = lat[std::min(lat.size() - 1, (size_t)(0.99 * (double)lat.size()))];
     }
     out->train_ms_mean = frames ? train_ms / frames : 0.0;
+    out->query_ms_mean = frames ? query_ms / frames : 0.0;
+    out->advance_ms_mean = frames ? adv_ms / frames : 0.0;
     out->frame_ms_mean = frames ? ms / frames : 0.0;
     cudaMemcpy(&out->last_loss, w->loss, 4, cudaMemcpyDeviceToHost);
     return NPM_OK;

@@ -63,11 +63,12 @@ npm_status tc_create(npm_handle* h);
 void tc_destroy(npm_handle* h);
 cudaError_t tc_refresh_weights(npm_handle* h, cudaStream_t st);
 cudaError_t tc_query_batch(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStream_t st);
-// Training step kernels on tensor cores (single-pass BF16 operands).
+// Training step kernels on tensor cores (split BF16 operands).
 bool tc_can_train(npm_handle* h);
 cudaError_t tc_train(npm_handle* h, int64_t n, int64_t ld, const float* pos, const float* aux, const float* dir,
                      const float* rad, const float* spdf, const float* dlogv, float* loss, cudaStream_t st);
+// log_pdf (evaluation only): pdf_out receives log V instead of V.
 npm_status tc_query(npm_handle* h, int64_t n, int64_t ld, const float* pos, const float* aux,
                     const float* uin, float ufrac, bool sample, float* dir_out, float* pdf_out,
-                    float* mix_out, cudaStream_t st);
+                    float* mix_out, cudaStream_t st, bool log_pdf = false);
 }  // namespace npm

@@ -52,11 +52,15 @@ size_t fwd_smem_bytes(const DevCfg& c);
 int carveout_percent(size_t bytes);
 size_t train_smem_bytes(const DevCfg& c);
 
+// wait_free: use only the tile-group kernel, which has no kernel-internal
+// waits (no mailbox hand-offs), so no launch can end early on a timeout.
+// log_pdf (evaluation only): pdf_out receives log V instead of V.
 cudaError_t launch_forward_fp32(const DevCfg& cfg, const float* grid, const float* wfwd, int64_t n,
                                 int64_t ld, const float* pos, const float* aux, const float* uin,
                                 float ufrac, bool sample, float* dir_out, float* pdf_out,
                                 float* mix_out, cudaStream_t st, int* status = nullptr,
-                                long long wait_limit = kDefaultWaitLimit);
+                                long long wait_limit = kDefaultWaitLimit, bool wait_free = false,
+                                bool log_pdf = false);
 
 // Several requests in one launch (segment table; tile offsets filled in
 // here). max_n bounds the device-side count when qb.n_dev is set. status
@@ -65,7 +69,8 @@ cudaError_t launch_forward_fp32(const DevCfg& cfg, const float* grid, const floa
 // non-blocking test per wait).
 cudaError_t launch_forward_fp32_batch(const DevCfg& cfg, const float* grid, const float* wfwd,
                                       QueryBatch& qb, int64_t max_n, cudaStream_t st,
-                                      int* status = nullptr, long long wait_limit = kDefaultWaitLimit);
+                                      int* status = nullptr, long long wait_limit = kDefaultWaitLimit,
+                                      bool wait_free = false);
 
 cudaError_t launch_train_fp32(const DevCfg& cfg, const float* params, int64_t mlp_off,
                               const float* wfwd, const float* wbwd, int64_t n, int64_t ld,

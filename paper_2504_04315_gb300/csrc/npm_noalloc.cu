@@ -7,8 +7,6 @@
 // fixed, file-scope device array, so the call needs no handle and performs
 // no allocation. The array is loaded with the library on every GPU that uses
 // it and stays resident until the process exits.
-#include <mutex>
-
 #include "npm_handle.h"
 #include "npm_kernels.h"
 
@@ -18,30 +16,19 @@ namespace {
 // NPM_NOALLOC_MAX_WEIGHT_FLOATS limit of include/npm.h.
 static __device__ __align__(256) float g_noalloc_weights[NPM_NOALLOC_MAX_WEIGHT_FLOATS];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-float* g_scratch[kMaxDevices] = {};
-
-// Per-device set-up: the device address of the scratch array. In host code
-// the array's name is only a host-side stand-in, so the address must come
-// from cudaGetSymbolAddress with the device current.
+// The device address of the scratch array on the current device. In host
+// code the array's name is only a host-side stand-in, so the address comes
+// from cudaGetSymbolAddress with the device current. It is looked up on
+// every call (a table lookup once the module is loaded; it allocates
+// nothing), so a context that was reset and re-created gets its own address.
 npm_status scratch_for_current_device(float** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return npm::set_error(NPM_ERR_CUDA, "cudaGetDevice failed");
-    if (dev < 0 || dev >= kMaxDevices)
-        return npm::set_error(NPM_ERR_UNSUPPORTED, "device index beyond the scratch table");
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_weights);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return npm::set_error(NPM_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
-        }
-        g_scratch[dev] = static_cast<float*>(p);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_weights);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return npm::set_error(NPM_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
     }
-    *out = g_scratch[dev];
+    *out = static_cast<float*>(p);
     return NPM_OK;
 }
 
@@ -87,8 +74,11 @@ extern "C" npm_status npm_eval_pdf_noalloc(const npm_config* cfg, const float* p
     k_noalloc_arrange<<<8, 256, 0, st>>>(dc, params + ng, scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return npm::set_error(NPM_ERR_CUDA, cudaGetErrorString(e));
+    // The tile-group kernel only: it has no kernel-internal waits, so no
+    // launch can give up part-way, and with no status word to report such
+    // an outcome every pdf_out value is written when the call succeeds.
     e = npm::launch_forward_fp32(dc, params, scratch, n, ld, pos, aux, dir, 0.0f, false, nullptr,
-                                 pdf_out, nullptr, st);
+                                 pdf_out, nullptr, st, nullptr, npm::kDefaultWaitLimit, true);
     if (e != cudaSuccess) return npm::set_error(NPM_ERR_CUDA, cudaGetErrorString(e));
     return NPM_OK;
 }

@@ -488,7 +488,7 @@ __device__ __forceinline__ void tc_decode(const TcCfg& tc, const float (&raw)[4 
                                           bool valid, int64_t ld, const float* __restrict__ uin,
                                           float ufrac, bool sample, float* __restrict__ dir_out,
                                           float* __restrict__ pdf_out,
-                                          float* __restrict__ mix_out) {
+                                          float* __restrict__ mix_out, bool log_pdf) {
     const DevCfg& cfg = tc.base;
     const int K = KEXACT ? KMAX : cfg.K;
     Lobe lob[KMAX];
@@ -557,10 +557,30 @@ __device__ __forceinline__ void tc_decode(const TcCfg& tc, const float (&raw)[4 
         w[2] = uin[2 * ld + j];
     }
     float pv = 0.0f;
+    if (!sample && log_pdf) {
+        // log V (Eq. 4 in log-sum-exp form), the weights' logs taken from
+        // the logits so that they stay finite where lambda_i underflows.
+        const float lnorm = mx + __logf(ssum);
+        float a[KMAX];
+        float m = -INFINITY;
 #pragma unroll
-    for (int i = 0; i < KMAX; ++i)
-        if (i < K) pv += lob[i].lam * vmf_eval_fast(lob[i], cn[i], w[0], w[1], w[2]);
-    if (sample && ufrac > 0.0f) pv = ufrac * kInv4Pi + (1.0f - ufrac) * pv;
+        for (int i = 0; i < KMAX; ++i)
+            if (i < K) {
+                const float d = lob[i].mu[0] * w[0] + lob[i].mu[1] * w[1] + lob[i].mu[2] * w[2];
+                a[i] = (raw[4 * i] - lnorm) + __logf(cn[i]) + lob[i].kap * (d - 1.0f);
+                m = fmaxf(m, a[i]);
+            }
+        float s = 0.0f;
+#pragma unroll
+        for (int i = 0; i < KMAX; ++i)
+            if (i < K) s += __expf(a[i] - m);
+        pv = m + __logf(s);
+    } else {
+#pragma unroll
+        for (int i = 0; i < KMAX; ++i)
+            if (i < K) pv += lob[i].lam * vmf_eval_fast(lob[i], cn[i], w[0], w[1], w[2]);
+        if (sample && ufrac > 0.0f) pv = ufrac * kInv4Pi + (1.0f - ufrac) * pv;
+    }
     if (valid) {
         if (sample) {
             dir_out[j] = w[0];
@@ -749,7 +769,8 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 
         for (int c = 0; c < 4 * KMAX / 16; ++c)
 #pragma unroll
             for (int i = 0; i < 16; ++i) rawf[c * 16 + i] = __uint_as_float(raw[c][i]);
-        tc_decode<KMAX, (NL > 0)>(tc, rawf, j, valid, ld, S.uin, S.ufrac, qb.sample != 0, S.dir, S.pdf, S.mix);
+        tc_decode<KMAX, (NL > 0)>(tc, rawf, j, valid, ld, S.uin, S.ufrac, qb.sample != 0, S.dir, S.pdf, S.mix,
+                                  qb.log_pdf != 0);
     }
     if (!ok) {
         if (t == 0) atomicOr(status, kStatusTimeout);
@@ -1343,10 +1364,14 @@ __global__ void __launch_bounds__(kTrainThreads, train_ctas_per_sm(KMAX, F2)) k_
 struct TcState {
     TcCfg cfg;
     uint8_t* wblob = nullptr;      // BF16 weights of the training parameters
+    // Training always multiplies split operands (BF16 high part and
+    // residual): with single-pass BF16 inference (NPM_BF16) this is a second
+    // blob in the split layout; otherwise training reads wblob.
+    uint8_t* wblob_train = nullptr;
     uint8_t* wblob_inf = nullptr;  // of the moving average, when inference uses it
     size_t smem = 0;
     int grid = 0;
-    TcCfg train_cfg;     // single-pass BF16 copy of cfg for training
+    TcCfg train_cfg;     // copy of cfg for training (split operands)
     TcTrain train;
     bool can_train = false;
     // Grid features of a training batch (max_batch x grid_feats FP32) for
@@ -1407,12 +1432,15 @@ npm_status tc_create(npm_handle* h) {
         delete s;
         return NPM_ERR_UNSUPPORTED;
     }
-    // Training layout (single-pass BF16 operands).
+    // Training layout. Gradients take split BF16 operands in both
+    // reduced-precision modes: single-pass BF16 compounds its rounding down
+    // the layers and through the cancelling grid sums (per-tensor gradient
+    // errors of tens of percent), so only inference offers the plain form.
     {
         TcTrain& tr = s->train;
         memset(&tr, 0, sizeof(tr));
         s->train_cfg = t;
-        uint32_t off = (c.precision == NPM_BF16X3 ? 2u : 1u) * t.w_bytes, col0 = 0, cols = 0;
+        uint32_t off = 2u * t.w_bytes, col0 = 0, cols = 0;
         int64_t wo = 0;
         bool fits = c.K * 4 <= 64 && c.n_levels * c.feat_per_level <= 32;
         for (int l = 0; l < c.n_layers; ++l) {
@@ -1430,7 +1458,7 @@ npm_status tc_create(npm_handle* h) {
             tr.idesc_dx[l] = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) |
                              ((uint32_t)(ly.Kp >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
         }
-        tr.split = c.precision == NPM_BF16X3 ? 1 : 0;
+        tr.split = 1;
         int maxkp = 0;
         for (int l = 0; l < c.n_layers; ++l) maxkp = std::max(maxkp, t.layer[l].Kp);
         tr.hlo_off = off;  // one residual activation tile, reused layer by layer
@@ -1461,6 +1489,15 @@ npm_status tc_create(npm_handle* h) {
         return NPM_ERR_OOM;
     }
     cudaMemset(s->wblob, 0, nsplit * t.w_bytes);
+    if (s->can_train && !t.split) {
+        if (cudaMalloc(&s->wblob_train, 2u * t.w_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(s->wblob);
+            delete s;
+            return NPM_ERR_OOM;
+        }
+        cudaMemset(s->wblob_train, 0, 2u * t.w_bytes);
+    }
     if (s->can_train && c.feat_per_level == 2) {
         // Optional: without it the training kernel encodes in place.
         if (cudaMalloc(&s->enc, sizeof(float) * (size_t)c.max_batch * h->dc.grid_feats) != cudaSuccess) {
@@ -1476,6 +1513,7 @@ void tc_destroy(npm_handle* h) {
     if (!h->tc) return;
     if (h->tc->wblob) cudaFree(h->tc->wblob);
     if (h->tc->wblob_inf) cudaFree(h->tc->wblob_inf);
+    if (h->tc->wblob_train) cudaFree(h->tc->wblob_train);
     if (h->tc->enc) cudaFree(h->tc->enc);
     delete h->tc;
     h->tc = nullptr;
@@ -1484,6 +1522,7 @@ void tc_destroy(npm_handle* h) {
 cudaError_t tc_refresh_weights(npm_handle* h, cudaStream_t st) {
     TcState* s = h->tc;
     k_tc_weights<<<16, 256, 0, st>>>(s->cfg, h->params + h->mlp_off, s->wblob);
+    if (s->wblob_train) k_tc_weights<<<16, 256, 0, st>>>(s->train_cfg, h->params + h->mlp_off, s->wblob_train);
     if (h->ema) {
         if (!s->wblob_inf) {
             const size_t bytes = (s->cfg.split ? 2u : 1u) * (size_t)s->cfg.w_bytes;
@@ -1581,7 +1620,8 @@ static cudaError_t launch_train_tc(npm_handle* h, int64_t n, int64_t ld, const f
         if (e != cudaSuccess) return e;
         enc = s->enc;
     }
-    kern<<<g < 1 ? 1 : g, kTrainThreads, s->train.smem, st>>>(s->train_cfg, s->train, h->params, s->wblob, n, ld, pos,
+    const uint8_t* wb = s->wblob_train ? s->wblob_train : s->wblob;
+    kern<<<g < 1 ? 1 : g, kTrainThreads, s->train.smem, st>>>(s->train_cfg, s->train, h->params, wb, n, ld, pos,
                                                          aux, dir, rad, spdf, dlogv, 1.0f / (float)n, h->grads,
                                                          h->mlp_off, loss, status, enc);
     return cudaGetLastError();
@@ -1619,11 +1659,12 @@ cudaError_t tc_query_batch(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStr
 
 npm_status tc_query(npm_handle* h, int64_t n, int64_t ld, const float* pos, const float* aux,
                     const float* uin, float ufrac, bool sample, float* dir_out, float* pdf_out,
-                    float* mix_out, cudaStream_t st) {
+                    float* mix_out, cudaStream_t st, bool log_pdf) {
     QueryBatch qb;
     memset(&qb, 0, sizeof(qb));
     qb.nseg = 1;
     qb.sample = sample ? 1 : 0;
+    qb.log_pdf = (!sample && log_pdf) ? 1 : 0;
     QuerySeg& q = qb.seg[0];
     q.n = n;
     q.ld = ld;

@@ -32,10 +32,29 @@ def test_tc_roofline_picks_the_smallest_bound():
 def test_train_roofline_adds_adam_and_scatter_time():
     w = synth.PRODUCT_BF16
     pk = {"hbm_gbs": 7000.0}
-    up = {"l2_atomic_v2_gops": 200.0}
+    up = {"l2_atomic_v2_gops": 200.0, "l2_atomic_v4_gops": 180.0}
     n_params = 10_000_000
+    # Upper bound: every corner one two-wide atomic.
     r = bench.train_roofline(5e8, w, n_params, pk, up)
     step = 34.0 * n_params / 7000e9 + w.n_train * len(w.level_res) * 8 / 200e9
     assert r["peak"] == pytest.approx(w.n_train / step)
     assert r["frac"] == pytest.approx(5e8 * step / w.n_train)
-    assert r["atomics_per_sample"] == 128
+    assert r["atomics_per_step"]["per_sample"] == 128
+    # Counted operations: four-wide at their own rate.
+    n4, n2 = 3_000_000, 40_000_000
+    r = bench.train_roofline(5e8, w, n_params, pk, up, (n4, n2))
+    step = 34.0 * n_params / 7000e9 + n4 / 180e9 + n2 / 200e9
+    assert r["peak"] == pytest.approx(w.n_train / step)
+    assert r["bound_ms"]["scatter_l2_atomics"] == pytest.approx((n4 / 180e9 + n2 / 200e9) * 1e3)
+
+
+def test_serving_roofline_sums_queries_compaction_and_training():
+    w = synth.TINY_BF16
+    pk = {"hbm_gbs": 8000.0, "bf16_tflops": 2000.0}
+    up = {"mufu_gops": 10000.0}
+    sv = {"queries": 64 * 6_500_000, "frame_ms_mean": 0.7}
+    r = bench.serving_roofline(sv, w, 64, pk, up, sms=152, sm_mhz=2000.0, train_bound_s=20e-6)
+    q_s = 6_500_000 / (152 * 128 * 2000e6 / 300)
+    c_s = 8 * 6_500_000 / 8000e9
+    assert r["bound_ms_per_frame"] == pytest.approx((q_s + c_s + 20e-6) * 1e3)
+    assert r["frac"] == pytest.approx((q_s + c_s + 20e-6) / 0.7e-3)

@@ -4,25 +4,33 @@ against the FP64 oracle run with the FP32 master parameters.
 Bar for the reduced-precision path: relative density error at the
 GPU-sampled direction, denominator floored at 1e-2/(4 pi), at most 2e-2 at
 the 99.9th percentile. Split BF16 (NPM_BF16X3) meets it on every workload.
-Single-pass BF16 (NPM_BF16) is held to a looser 5e-2: on these sharp-lobe
-parameters (kappa up to ~35) the BF16 rounding of the lobe means alone is
-amplified to 1.5e-2 .. 4e-2.
+
+Single-pass BF16 inference (NPM_BF16) does not meet it on these sharp-lobe
+parameters (kappa up to ~35): its 8-bit significands put the density 1.5e-2
+to 6e-2 off at the 99.9th percentile. Its kernels are checked instead
+against a model of exactly that quantisation (tests/bf16_model.py: FP16
+table, BF16 operands rounded to nearest, FP32 sums), within 2e-3 at the
+99.9th percentile, and its distance from the oracle is printed. Training
+takes split operands in both reduced-precision modes and is held to the
+2e-2 gradient bar.
 """
 import math
 
 import numpy as np
 import pytest
 
+import bf16_model
 import oracle
 import synth
-from gpu_helpers import PRODUCT_SMALL, cuda, host, make_model
+from gpu_helpers import PRODUCT_SMALL, compare_rp_directions, cuda, host, make_model
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
 PDF_P999_BF16 = 2e-2
-PDF_P999_BF16_SINGLE = 5e-2
+# Single-pass BF16 against the model of its own operand rounding.
+PDF_P999_BF16_MODEL = 2e-3
 FLOOR = 1e-2 / (4 * math.pi)
 
 
@@ -50,21 +58,35 @@ def _bf16_stats(w, n, seed, params=None, precision=synth.BF16X3):
     return err, gm, om, m, params, pos, aux
 
 
-@pytest.mark.parametrize("n", [1, 128, 1000])
-def test_tc_small_tiny(n):
-    err, gm, om, _, _, _, _ = _bf16_stats(synth.TINY_BF16, n, 21, precision=synth.BF16)
-    print(f"n={n} pdf err p50 {np.median(err):.2e} p99.9 {np.quantile(err, 0.999):.2e} max {err.max():.2e}")
-    assert np.quantile(err, 0.999) <= PDF_P999_BF16_SINGLE
-    # decoded weights match to BF16 accuracy
-    assert np.abs(gm[0::4] - om[0::4]).max() < 3e-2
+def _bf16_single_vs_model(n, seed, dirs=None):
+    """Single-pass BF16: density at the sampled (or given) directions
+    against the BF16 quantisation model; returns (error vs model, error vs
+    oracle)."""
+    w = synth.TINY_BF16.with_(precision=synth.BF16)
+    params = synth.random_params(w, seed)
+    pos = synth.positions(seed, n)
+    m = make_model(w, params, n, precision=synth.BF16)
+    if dirs is None:
+        d, p, _ = m.query_sample(cuda(pos), cuda(synth.sample_uniforms(seed, n)))
+        gd = host(d).astype(np.float64)
+    else:
+        gd = dirs.astype(np.float64)
+        p = m.eval_pdf(cuda(pos), cuda(dirs))
+    gp = host(p).astype(np.float64)
+    m.check_device_status()
+    model = bf16_model.density(w, bf16_model.raw_outputs(w, params, pos), gd)
+    ref = oracle.eval_pdf64(w, params, pos, gd)
+    e_model = np.abs(gp - model) / np.maximum(model, FLOOR)
+    e_oracle = np.abs(gp - ref) / np.maximum(ref, FLOOR)
+    print(f"bf16 n={n}: vs quantisation model p99.9 {np.quantile(e_model, 0.999):.2e} max {e_model.max():.2e}; "
+          f"vs oracle p99.9 {np.quantile(e_oracle, 0.999):.2e} (outside the 2e-2 bar is expected)")
+    return e_model, e_oracle
 
 
-@pytest.mark.parametrize("w,n", [(synth.TINY_BF16, 1 << 16)])
-def test_tc_pdf_parity(w, n):
-    err, gm, om, _, _, _, _ = _bf16_stats(w, n, 22, precision=synth.BF16)
-    print(f"{w.name[:30]} n={n} pdf err p50 {np.median(err):.2e} p99.9 "
-          f"{np.quantile(err, 0.999):.2e} max {err.max():.2e}")
-    assert np.quantile(err, 0.999) <= PDF_P999_BF16_SINGLE
+@pytest.mark.parametrize("n", [1, 128, 1000, 1 << 16])
+def test_tc_bf16_single_matches_quantisation_model(n):
+    e_model, _ = _bf16_single_vs_model(n, 21 if n < 4096 else 22)
+    assert np.quantile(e_model, 0.999) <= PDF_P999_BF16_MODEL
 
 
 @pytest.mark.parametrize("w,n", [(synth.TINY_BF16, 1 << 16),
@@ -82,11 +104,25 @@ def test_tc_split_bf16_parity(w, n):
     assert np.median(err) <= 1e-3
 
 
-@pytest.mark.parametrize("precision,dirs_from", [(synth.BF16, "mixture"), (synth.BF16X3, "mixture"),
-                                                 (synth.BF16X3, "uniform")])
-def test_tc_eval_pdf_matches_oracle(precision, dirs_from):
-    # Plain BF16 is held to the bar at directions drawn from the mixture
-    # (where the guide is used); split BF16 also at uniform directions.
+@pytest.mark.parametrize("dirs_from", ["mixture", "uniform"])
+def test_tc_bf16_single_eval_pdf_matches_quantisation_model(dirs_from):
+    n = 4096
+    if dirs_from == "uniform":
+        uu = synth.uniform_rows(23, synth.S_DIR, 2, n)
+        dirs = synth.sphere_dirs(uu[0], uu[1]).astype(np.float32)
+    else:
+        w = synth.TINY_BF16
+        dirs = oracle.query_sample(w, synth.random_params(w, 23), synth.positions(23, n),
+                                   synth.sample_uniforms(23, n))[0].astype(np.float32)
+    e_model, _ = _bf16_single_vs_model(n, 23, dirs=dirs)
+    assert np.quantile(e_model, 0.999) <= PDF_P999_BF16_MODEL
+
+
+@pytest.mark.parametrize("dirs_from", ["mixture", "uniform"])
+def test_tc_eval_pdf_matches_oracle(dirs_from):
+    # Split BF16 density at directions drawn from the mixture (where the
+    # guide is used) and uniformly.
+    precision = synth.BF16X3
     w = synth.TINY_BF16
     n = 4096
     params = synth.random_params(w, 23)
@@ -100,26 +136,8 @@ def test_tc_eval_pdf_matches_oracle(precision, dirs_from):
     got = host(m.eval_pdf(cuda(pos), cuda(dirs)))
     ref = oracle.eval_pdf(w, params, pos, dirs)
     err = np.abs(got - ref) / np.maximum(ref, FLOOR)
-    print(f"eval precision={precision} dirs={dirs_from}: p99.9 {np.quantile(err, 0.999):.2e}")
-    bar = PDF_P999_BF16 if precision == synth.BF16X3 else PDF_P999_BF16_SINGLE
-    assert np.quantile(err, 0.999) <= bar
-
-
-def test_tc_matches_fp32_path_on_lobe_choice():
-    # The BF16 path picks the same lobe as the FP32 path except near CDF
-    # boundaries: compare directions from both GPU paths.
-    w = synth.TINY_BF16
-    n = 1 << 14
-    params = synth.random_params(w, 24)
-    pos = synth.positions(24, n)
-    u = synth.sample_uniforms(24, n)
-    mb = make_model(w, params, n, precision=synth.BF16X3)
-    mf = make_model(w, params, n, precision=synth.FP32)
-    db, _, _ = mb.query_sample(cuda(pos), cuda(u))
-    df, _, _ = mf.query_sample(cuda(pos), cuda(u))
-    ang = np.linalg.norm(host(db) - host(df), axis=0)
-    assert np.median(ang) < 2e-2
-    assert (ang > 0.5).mean() < 2e-2
+    print(f"eval split bf16 dirs={dirs_from}: p99.9 {np.quantile(err, 0.999):.2e}")
+    assert np.quantile(err, 0.999) <= PDF_P999_BF16
 
 
 @pytest.mark.parametrize("w,n", [(synth.TINY_BF16, 4096), (PRODUCT_SMALL.with_(precision=synth.BF16X3), 4096),
@@ -128,10 +146,9 @@ def test_tc_matches_fp32_path_on_lobe_choice():
                                  (synth.PRODUCT_BF16, 3000),
                                  (synth.TINY_BF16.with_(precision=synth.BF16), 4096)])
 def test_tc_gradient_parity(w, n):
-    # Training on tensor cores (FP32 TMEM accumulation, FP16 grid features)
-    # against the FP64 oracle with the FP32 master parameters. Split BF16:
-    # per-tensor relative L2 <= 2e-2. Single-pass BF16 compounds its rounding
-    # down the layers and the grid sums cancel heavily: held to 0.3.
+    # Training on tensor cores (FP32 TMEM accumulation, split BF16
+    # operands in both reduced-precision modes) against the FP64 oracle
+    # with the FP32 master parameters: per-tensor relative L2 <= 2e-2.
     params = synth.random_params(w, 12)
     b = synth.train_batch_uniform(w, n, seed=12)
     m = make_model(w, params, n, precision=w.precision)
@@ -152,7 +169,7 @@ def test_tc_gradient_parity(w, n):
         errs[name] = np.linalg.norm(g[sl] - ref[sl]) / max(np.linalg.norm(ref[sl]), 1e-30)
     print(f"tc grad rel L2 {w.name[:30]} precision {w.precision}: "
           + ", ".join(f"{k} {v:.2e}" for k, v in errs.items()))
-    bar = 2e-2 if w.precision == synth.BF16X3 else 0.3
+    bar = 2e-2
     assert max(errs.values()) <= bar, errs
     # The training loss of the same batch through train_step.
     m2 = make_model(w, params, n, precision=w.precision)
@@ -191,8 +208,9 @@ def test_tc_kl_estimate_matches_oracle(w):
 
 def test_tc_tiny_full_size_launch_sampled():
     # The reduced-precision workload as the benchmark launches it: 2^22
-    # queries in one call, split BF16; the oracle checks a seeded 2^16 subset
-    # at the GPU-sampled directions.
+    # queries in one call, split BF16; the oracle checks a seeded 2^16 subset:
+    # the density at the GPU-sampled directions and the directions
+    # themselves (oracle.query_sample on the same uniforms).
     w = synth.TINY_BF16
     n = w.n_query
     params = synth.random_params(w, 3)
@@ -209,3 +227,4 @@ def test_tc_tiny_full_size_launch_sampled():
     err = np.abs(gp[pick] - ref) / np.maximum(ref, FLOOR)
     print(f"tiny 2^22 launch, 2^16 subset: p99.9 {np.quantile(err, 0.999):.2e} max {err.max():.2e}")
     assert np.quantile(err, 0.999) <= PDF_P999_BF16
+    compare_rp_directions(w, params, pos[:, pick], u[:, pick], None, gd[:, pick].astype(np.float64))

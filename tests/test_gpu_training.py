@@ -137,22 +137,42 @@ def test_product_workload_200_steps():
     assert mix_trained < 0.5 * rv_uniform
 
 
-def test_product_full_batch_gradient_matches_oracle():
-    # The product workload's full training batch (2^19 samples) through the
+_FULL_BATCH_REF = {}
+
+
+def _full_batch_ref(w, params, b):
+    key = id(params)
+    if key not in _FULL_BATCH_REF:
+        _FULL_BATCH_REF.clear()
+        _FULL_BATCH_REF[key] = oracle.train_grad(w, params, b.pos, b.dir, b.radiance, b.pdf, b.aux)[1]
+    return _FULL_BATCH_REF[key]
+
+
+_FULL_BATCH = {}
+
+
+@pytest.mark.parametrize("precision,bar", [(synth.BF16X3, 2e-2), (synth.FP32, 1e-4)],
+                         ids=["split-bf16", "fp32"])
+def test_product_full_batch_gradient_matches_oracle(precision, bar):
+    # The product workload's full training batch (2^19 samples, the batch
+    # the benchmark times) against the FP64 oracle with the FP32 master
+    # parameters, per-tensor relative L2 of the gradient: <= 2e-2 through the
     # tensor-core training path (encode kernel, training kernel with each
     # tile's grid scatter issued during the next tile's MMAs, many tiles per
-    # CTA): per-tensor relative L2 of the gradient <= 2e-2 against the FP64
-    # oracle with the FP32 master parameters.
+    # CTA) and <= 1e-4 through the FP32 training kernel (many 64-sample
+    # tiles per CTA, grid atomics from every tile).
     w = synth.PRODUCT_BF16
     n = w.n_train
-    params = synth.random_params(w, 12)
-    b = synth.train_batch_uniform(w, n, seed=12)
-    m = make_model(w, params, n, precision=w.precision)
+    if not _FULL_BATCH:
+        _FULL_BATCH["params"] = synth.random_params(w, 12)
+        _FULL_BATCH["batch"] = synth.train_batch_uniform(w, n, seed=12)
+    params, b = _FULL_BATCH["params"], _FULL_BATCH["batch"]
+    m = make_model(w, params, n, precision=precision)
     dlogv = -(b.radiance.astype(np.float64) / b.pdf) / n
     m.backward(cuda(b.pos), cuda(b.dir), cuda(dlogv), cuda(b.aux))
     g = m.get_grads().astype(np.float64)
     m.check_device_status()
-    _, ref = oracle.train_grad(w, params, b.pos, b.dir, b.radiance, b.pdf, b.aux)
+    ref = _full_batch_ref(w, params, b)
     ng = sum(synth.grid_sizes(w)) * w.feat
     blocks = [("grid", slice(0, ng))]
     o = ng
@@ -161,5 +181,6 @@ def test_product_full_batch_gradient_matches_oracle():
         blocks.append((f"W{i + 1}", slice(o, o + k)))
         o += k
     errs = {name: np.linalg.norm(g[sl] - ref[sl]) / max(np.linalg.norm(ref[sl]), 1e-30) for name, sl in blocks}
-    print("full-batch product gradient rel L2: " + ", ".join(f"{k} {v:.2e}" for k, v in errs.items()))
-    assert max(errs.values()) <= 2e-2, errs
+    print(f"full-batch product gradient rel L2 (precision {precision}): "
+          + ", ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+    assert max(errs.values()) <= bar, errs

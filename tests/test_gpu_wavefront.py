@@ -41,5 +41,15 @@ def test_graph_replay_matches_eager(precision):
     assert abs(a["queries"] - expect) < 0.01 * expect
     assert math.isfinite(a["last_loss"]) and abs(a["last_loss"] - b["last_loss"]) <= 1e-4 * abs(a["last_loss"])
     assert b["bounce_p99_ms"] >= b["bounce_p50_ms"] > 0 and b["train_ms_mean"] > 0
+    # The per-bounce breakdown: live paths per bounce add up to the queries
+    # served, shrink bounce by bounce, and the frame's parts fit in its time.
+    for st in (a, b):
+        assert abs(sum(st["bounce_queries"]) * frames - st["queries"]) < 1e-6 * st["queries"]
+        assert st["bounce_queries"][0] == P
+        assert all(x > y for x, y in zip(st["bounce_queries"], st["bounce_queries"][1:]))
+        assert all(t > 0 for t in st["bounce_query_ms"])
+        assert abs(sum(st["bounce_query_ms"]) - st["query_ms_mean"]) < 1e-6 + 1e-6 * st["query_ms_mean"]
+        parts = st["query_ms_mean"] + st["advance_ms_mean"] + st["train_ms_mean"]
+        assert 0 < parts <= st["frame_ms_mean"] * 1.001
     # Same training trajectory up to the summation order of gradient atomics.
     assert (np.abs(a["params"] - b["params"]) < 1e-5).mean() > 0.999

@@ -10,8 +10,9 @@ import os
 import mpmath
 import numpy as np
 import pytest
-from scipy import optimize, special, stats
+from scipy import optimize, special
 
+import mixtures
 import oracle
 import synth
 
@@ -243,35 +244,10 @@ def test_vmf_normaliser_closed_form(k):
     assert abs(mpmath.mpf(got) / ref - 1) < 1e-13
 
 
-def _diverse_params(w, raw_target, x):
-    """Parameters whose network outputs exactly raw_target at position x:
-    constant grid features, random hidden layers, and a last layer solved so
-    that its outputs equal the target."""
-    rng = np.random.default_rng(8)
-    npar = oracle.n_params(w)
-    params = rng.standard_normal(npar) * 0.5
-    ng = npar - sum(a * b for a, b in zip(w.widths[:-1], w.widths[1:]))
-    params[:ng] = np.tile([1.0, 0.5, -0.3, 0.8][: w.feat], ng // w.feat)
-    enc = oracle.encode(w, params, np.asarray(x, np.float32))
-    _, acts = oracle.mlp(w, params, enc, want_acts=True)
-    h = np.maximum(acts[-(w.widths[-1] + w.widths[-2]):-w.widths[-1]], 0.0)
-    last = npar - w.widths[-1] * w.widths[-2]
-    W = np.outer(raw_target, h) / np.dot(h, h)
-    params[last:] = W.ravel()
-    return params
-
-
-def _raw_for(lams, kaps, thetas, phis):
-    raw = []
-    for l, k, t, p in zip(lams, kaps, thetas, phis):
-        raw += [math.log(l), math.log(math.expm1(k)), special.logit(t / math.pi),
-                special.logit(p / (2 * math.pi))]
-    return np.array(raw)
-
-
-MIX = dict(lams=[0.4, 0.3, 0.2, 0.1], kaps=[2.0, 20.0, 50.0, 0.5],
-           thetas=[0.4, 2.0, 1.2, 2.9], phis=[0.3, 4.0, 2.5, 5.9])
-X0 = [0.31, 0.62, 0.17]
+_diverse_params = mixtures.diverse_params
+_raw_for = mixtures.raw_for
+MIX = mixtures.MIX
+X0 = mixtures.X0
 
 
 def test_mixture_decodes_to_target():
@@ -339,39 +315,13 @@ def _chi2_sampling(w, params, alpha, n=1_000_000, seed=11, sample_params=None):
     sp = params if sample_params is None else sample_params
     d, pdf, _, _ = oracle.query_sample(w, sp, pos, u, alpha=alpha)
     assert np.abs(np.linalg.norm(d, axis=0) - 1.0).max() < 1e-12
-    nz, nph = 64, 128
-    z = np.clip(d[2], -1, 1)
-    ph = np.mod(np.arctan2(d[1], d[0]), 2 * math.pi)
-    bz = np.minimum(((z + 1) / 2 * nz).astype(int), nz - 1)
-    bp = np.minimum((ph / (2 * math.pi) * nph).astype(int), nph - 1)
-    obs = np.bincount(bz * nph + bp, minlength=nz * nph).astype(float)
-    # Expected counts: density integrated over each bin by 6x6 Gauss-Legendre.
-    g, gw = np.polynomial.legendre.leggauss(6)
-    zc = (np.arange(nz) + 0.5) / nz * 2 - 1
-    pc = (np.arange(nph) + 0.5) / nph * 2 * math.pi
-    hz, hp = 1.0 / nz, math.pi / nph
-    Z = (zc[:, None] + hz * g[None, :]).ravel()
-    P = (pc[:, None] + hp * g[None, :]).ravel()
-    ZZ, PP = np.meshgrid(Z, P, indexing="ij")
-    r = np.sqrt(np.clip(1 - ZZ ** 2, 0, None))
-    dirs = np.stack([r * np.cos(PP), r * np.sin(PP), ZZ]).reshape(3, -1)
-    npts = dirs.shape[1]
-    posq = np.repeat(np.array(X0, np.float32)[:, None], npts, axis=1)
-    v = oracle.eval_pdf64(w, params, posq, dirs)
-    dens = alpha / (4 * math.pi) + (1 - alpha) * v
-    dens = dens.reshape(nz, 6, nph, 6)
-    wgt = (gw[:, None] * gw[None, :]) * hz * hp
-    exp_c = np.einsum("aibj,ij->ab", dens, wgt).ravel() * n
-    assert abs(exp_c.sum() / n - 1.0) < 1e-6
-    keep = exp_c >= 5
-    pooled_o, pooled_e = obs[~keep].sum(), exp_c[~keep].sum()
-    o = np.append(obs[keep], pooled_o)
-    e = np.append(exp_c[keep], pooled_e)
-    if pooled_e < 5:
-        o, e = obs[keep], exp_c[keep]
-    chi2 = ((o - e) ** 2 / e).sum()
-    dof = len(o) - 1
-    return stats.chi2.sf(chi2, dof), pdf, d
+
+    def density(dirs):
+        posq = np.repeat(np.array(X0, np.float32)[:, None], dirs.shape[1], axis=1)
+        return alpha / (4 * math.pi) + (1 - alpha) * oracle.eval_pdf64(w, params, posq, dirs)
+
+    p, _ = mixtures.chi2_directions(d, density)
+    return p, pdf, d
 
 
 @pytest.mark.parametrize("alpha", [0.0, 0.5])

@@ -1,8 +1,9 @@
 """npm_eval_pdf_noalloc: the allocation-free density evaluation for callers
 that cannot allocate device memory (a renderer with its own allocator, a
 plug-in that may not call cudaMalloc during a frame). It must give the same
-densities as npm_eval_pdf on a handle with the same parameters, call after
-call, although every call shares one static scratch array.
+densities as npm_eval_pdf on a handle with the same parameters and as the
+FP64 oracle, call after call, although every call shares one static scratch
+array.
 
 This file is collected last so that a run stopping at its first failure has
 already run every other test."""
@@ -11,6 +12,7 @@ import ctypes as C
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from gpu_helpers import PDF_RTOL_FP32, PRODUCT_SMALL, cuda, host, make_model
 
@@ -39,22 +41,29 @@ def _case(w, n, seed):
     m = make_model(w, params, n, precision=synth.FP32)
     ref = host(m.eval_pdf(cuda(pos), cuda(dirs), None if aux is None else cuda(aux)))
     m.close()
+    orc = oracle.eval_pdf(w, params, pos, dirs, aux)
     cfg = npm.config_from(w, max_batch=n, precision=synth.FP32)
-    return cfg, cuda(params), cuda(pos), cuda(dirs), None if aux is None else cuda(aux), ref
+    return cfg, cuda(params), cuda(pos), cuda(dirs), None if aux is None else cuda(aux), ref, orc
 
 
 def test_noalloc_matches_eval_pdf_two_calls_in_a_row():
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
-    cases = [_case(synth.TINY, 4096 + 37, 31), _case(PRODUCT_SMALL, 3000, 32)]
-    # Two calls in a row on different models: the second overwrites the
-    # shared scratch left by the first. Then the first model again.
-    for cfg, p, pos, dirs, aux, ref in cases + cases[:1]:
+    # The tiny model, a product-mode model and the paper-shaped hash grid
+    # (16 levels, 32-64-64-64-32, K = 8: 12,288 padded weight floats, the
+    # network on which npm_eval_pdf runs the warp-specialised kernel).
+    cases = [_case(synth.TINY, 4096 + 37, 31), _case(PRODUCT_SMALL, 3000, 32),
+             _case(synth.PAPER_HASH, 5000, 33)]
+    # Calls in a row on different models: each overwrites the shared
+    # scratch left by the one before. Then the first model again.
+    for cfg, p, pos, dirs, aux, ref, orc in cases + cases[:1]:
         out = torch.full((pos.shape[1],), -1.0, device="cuda")
         _noalloc(cfg, p, pos, dirs, aux, out)
         got = host(out)
         err = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-30)
         assert err.max() <= PDF_RTOL_FP32, err.max()
+        err_o = np.abs(got - orc) / np.maximum(np.abs(orc), 1e-30)
+        assert err_o.max() <= PDF_RTOL_FP32, err_o.max()
 
 
 def test_noalloc_rejects_weights_beyond_the_limit():
