@@ -190,49 +190,100 @@ __device__ __forceinline__ float2 pair_log_terms(const LobePair& L, float2 logit
     return make_float2(logit.x - lnorm + kLn2 * hw_lg2(cn.x) - e.x, logit.y - lnorm + kLn2 * hw_lg2(cn.y) - e.y);
 }
 
+// Tile groups per CTA: one CTA per SM, each group of 128 threads walks its
+// own tiles with its own activation tile, tensor-memory columns, MMA
+// barrier and named CTA barrier, sharing one copy of the weights and of the
+// grid table in shared memory.
+constexpr int kGroups = 8;
+
+// Named barrier of group g (id 0 is the CTA-wide __syncthreads).
+__device__ __forceinline__ void group_sync(int g) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kThreads) : "memory");
+}
+// Barrier of group g that also ORs a predicate over its threads.
+__device__ __forceinline__ bool group_sync_or(int g, bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred q, o;\n\t"
+        "setp.ne.u32 q, %3, 0;\n\t"
+        "bar.red.or.pred o, %1, %2, q;\n\t"
+        "selp.u32 %0, 1, 0, o;\n\t}\n"
+        : "=r"(r)
+        : "r"(1 + g), "r"(kThreads), "r"((uint32_t)p)
+        : "memory");
+    return r != 0;
+}
+
+// Shared-memory layout of the CTA (byte offsets).
+struct TinyLayout {
+    uint32_t grid, a, a_stride, bars, bytes;
+};
+
+__host__ __device__ inline TinyLayout tiny_layout(const TcCfg& c, uint32_t grid_bytes) {
+    TinyLayout L;
+    const uint32_t nsplit = c.split ? 2u : 1u;
+    L.grid = nsplit * c.w_bytes;                            // weights first (hi, then lo)
+    L.a = (L.grid + grid_bytes + 1023u) & ~1023u;           // per-group activation tiles
+    L.a_stride = nsplit * c.a_bytes;                        // hi tile, then its residual
+    L.bars = L.a + (uint32_t)kGroups * L.a_stride;          // [0] weights + grid, [1 + g] MMA
+    L.bytes = L.bars + 8u * (1u + kGroups) + 16u;           // + tensor-memory slot
+    return L;
+}
+
 template <bool SPLIT>
-__global__ void __launch_bounds__(kThreads, 8) k_forward_tiny(const __grid_constant__ TcCfg tc,
-                                                             const uint2* __restrict__ grid4,
-                                                             const uint8_t* __restrict__ wblob,
-                                                             const __grid_constant__ QueryBatch qb,
-                                                             int* __restrict__ status) {
+__global__ void __launch_bounds__(kThreads * kGroups, 1) k_forward_tiny(const __grid_constant__ TcCfg tc,
+                                                                        const uint2* __restrict__ grid4,
+                                                                        uint32_t grid_bytes,
+                                                                        const uint8_t* __restrict__ wblob,
+                                                                        const __grid_constant__ QueryBatch qb,
+                                                                        int* __restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem[];
     constexpr int nsplit = SPLIT ? 2 : 1;
+    const TinyLayout lay = tiny_layout(tc, grid_bytes);
+    const int g = threadIdx.x >> 7;      // tile group
+    const int t = threadIdx.x & 127;     // row of the group's tile
+    const int warp = t >> 5;             // warp within the group (its TMEM lane quarter)
     uint8_t* sW = smem;
-    uint8_t* sA = smem + nsplit * tc.w_bytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sA + nsplit * tc.a_bytes);  // [0] mma, [1] weights
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
-    const int t = threadIdx.x;
-    const int warp = t >> 5;
-    const uint32_t bar_mma = smem_u32(&bars[0]);
-    const uint32_t bar_w = smem_u32(&bars[1]);
+    const uint2* sG = reinterpret_cast<const uint2*>(smem + lay.grid);
+    uint8_t* sA = smem + lay.a + (uint32_t)g * lay.a_stride;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + lay.bars);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 1 + kGroups);
+    const uint32_t bar_w = smem_u32(&bars[0]);
+    const uint32_t bar_mma = smem_u32(&bars[1 + g]);
 
-    if (warp == 0) {
+    if (threadIdx.x < 32) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"(tc.tmem_cols)
+                     "r"(32u * kGroups)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (t == 0) {
-        mbar_init(bar_mma, 1);
-        mbar_init(bar_w, 1);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i <= kGroups; ++i) mbar_init(smem_u32(&bars[i]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *tslot;
-    if (t == 0) {
+    // This group's 32 tensor-memory columns.
+    const uint32_t tmem = *tslot + 32u * (uint32_t)g;
+    if (threadIdx.x == 0) {
+        // Weights and grid table: two bulk copies on one barrier.
         const uint32_t wb = (uint32_t)nsplit * tc.w_bytes;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_w), "r"(wb) : "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_w), "r"(wb + grid_bytes)
+                     : "memory");
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                 smem_u32(sW)),
             "l"(wblob), "r"(wb), "r"(bar_w)
             : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(smem + lay.grid)),
+            "l"(grid4), "r"(grid_bytes), "r"(bar_w)
+            : "memory");
     }
-    bool ok = !__syncthreads_or(warp == 0 && !mbar_wait_bounded(bar_w, 0));
+    bool ok = !__syncthreads_or(threadIdx.x < 32 && !mbar_wait_bounded(bar_w, 0));
     uint32_t phase = 0;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     // This thread's row in the K-major activation tile: 16-column layout
@@ -250,7 +301,8 @@ __global__ void __launch_bounds__(kThreads, 8) k_forward_tiny(const __grid_const
         n0 = *qb.n_dev;
         ntiles = (n0 + kTile - 1) / kTile;
     }
-    for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * kGroups;
+    for (int64_t tile = (int64_t)blockIdx.x * kGroups + g; ok && tile < ntiles; tile += stride) {
         int sg = 0;
         while (sg + 1 < qb.nseg && tile >= qb.seg[sg + 1].tile0) ++sg;
         const QuerySeg& S = qb.seg[sg];
@@ -260,13 +312,13 @@ __global__ void __launch_bounds__(kThreads, 8) k_forward_tiny(const __grid_const
         const bool valid = j < n;
         if (warp == 3) {
             // Into L2 while this tile is encoded and run through the MLP: its
-            // uniforms (or directions) and the next tile's positions.
+            // uniforms (or directions) and the group's next tile's positions.
             const int lane = t & 31, r = lane >> 2;
             const int64_t b0 = (tile - S.tile0) * kTile + 32 * (lane & 3);
             if (r < 4) {
                 if ((r < 3 || S.ufrac > 0.0f) && b0 < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(S.uin + r * ld + b0));
             } else if (r < 7) {
-                const int64_t nt = tile + gridDim.x;
+                const int64_t nt = tile + stride;
                 if (nt < ntiles) {
                     int s2 = sg;
                     while (s2 + 1 < qb.nseg && nt >= qb.seg[s2 + 1].tile0) ++s2;
@@ -277,9 +329,10 @@ __global__ void __launch_bounds__(kThreads, 8) k_forward_tiny(const __grid_const
                 }
             }
         }
-        // ---- encode (Sec. 5.1, Eq. 11): the 8 corners of the cell, blended
-        // in FP32, written as this row's first 8-column chunk (4 features,
-        // 4 zeros); the second chunk of the 16-column input is zero.
+        // ---- encode (Sec. 5.1, Eq. 11): the 8 corners of the cell from the
+        // shared-memory table, blended in FP32, written as this row's first
+        // 8-column chunk (4 features, 4 zeros); the second chunk of the
+        // 16-column input is zero.
         {
             float x = 0.0f, y = 0.0f, z = 0.0f;
             if (valid) {
@@ -291,8 +344,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_forward_tiny(const __grid_const
             const uint32_t b = cl.c[0] + uD * (cl.c[1] + uD * cl.c[2]);
             uint2 raw[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-                raw[c] = __ldg(grid4 + (b + (c & 1) + ((c & 2) ? uD : 0u) + ((c & 4) ? uD2 : 0u)));
+            for (int c = 0; c < 8; ++c) raw[c] = sG[b + (c & 1) + ((c & 2) ? uD : 0u) + ((c & 4) ? uD2 : 0u)];
             float w8[8];
             corner_w8(cl, w8);
             float2 a01 = make_float2(0.0f, 0.0f), a23 = make_float2(0.0f, 0.0f);
@@ -315,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_forward_tiny(const __grid_const
         }
         fence_async_smem();
         tc_fence_before();
-        __syncthreads();
+        group_sync(g);
         uint32_t rawu[16];
 #pragma unroll
         for (int l = 0; l < 3; ++l) {
@@ -335,9 +387,11 @@ __global__ void __launch_bounds__(kThreads, 8) k_forward_tiny(const __grid_const
                 }
                 mma_commit(bar_mma);
             }
+            // Warp 0 of the group waits on the MMA barrier; the group's other
+            // warps wait in its named barrier, which also passes the outcome.
             const bool done = warp != 0 || mbar_wait_bounded(bar_mma, phase);
             phase ^= 1u;
-            ok = !__syncthreads_or(!done);
+            ok = !group_sync_or(g, !done);
             if (!ok) break;
             tc_fence_after();
             if (l < 2) {
@@ -365,7 +419,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_forward_tiny(const __grid_const
                 }
                 fence_async_smem();
                 tc_fence_before();
-                __syncthreads();
+                group_sync(g);
             } else {
                 tmem_ld16(tmem + lane_base, rawu);
                 tmem_wait16(rawu);
@@ -451,19 +505,19 @@ __global__ void __launch_bounds__(kThreads, 8) k_forward_tiny(const __grid_const
     }
     if (!ok) {
         if (t == 0) atomicOr(status, kStatusTimeout);
-        // Drain this CTA's own asynchronous work (bounded) before the tensor
-        // memory is released: the weights' bulk copy and the MMA batch whose
-        // wait gave up.
+        // Drain this group's own asynchronous work (bounded) before the
+        // tensor memory is released: the MMA batch whose wait gave up (and,
+        // for group 0, the weights' and grid's bulk copies).
         if (warp == 0) {
-            (void)mbar_wait_bounded(bar_w, 0);
+            if (g == 0) (void)mbar_wait_bounded(bar_w, 0);
             (void)mbar_wait_bounded(bar_mma, phase ^ 1u);
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (threadIdx.x < 32) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tc.tmem_cols)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(32u * kGroups)
                      : "memory");
     }
 }
@@ -472,23 +526,23 @@ __global__ void __launch_bounds__(kThreads, 8) k_forward_tiny(const __grid_const
 
 bool tiny_qualifies(const TcCfg& c) {
     const DevCfg& d = c.base;
+    const uint32_t grid_bytes = (uint32_t)d.level_res[0] * d.level_res[0] * d.level_res[0] * 8u;
     return d.mode == NPM_RADIANCE && d.n_levels == 1 && d.feat == 4 && (d.dense_mask & 1u) && d.n_layers == 3 &&
            d.K == 4 && d.kappa_act == NPM_SOFTPLUS && c.layer[0].Kp == 16 && c.layer[0].Np <= 32 &&
            c.layer[1].Kp == 32 && c.layer[1].Np <= 32 && c.layer[2].Kp == 32 && c.layer[2].Np == 16 &&
-           c.a0_bytes == 0 && c.a_bytes == (uint32_t)(kTile * 32 * 2) && c.tmem_cols >= 32;
+           c.a0_bytes == 0 && c.a_bytes == (uint32_t)(kTile * 32 * 2) && grid_bytes % 16u == 0 &&
+           tiny_layout(c, grid_bytes).bytes <= 227u * 1024u;
 }
 
-cudaError_t launch_tiny(const TcCfg& c, size_t smem, const __half* grid_h, const uint8_t* wblob, QueryBatch& qb,
+cudaError_t launch_tiny(const TcCfg& c, size_t, const __half* grid_h, const uint8_t* wblob, QueryBatch& qb,
                         int64_t max_n, int* status, cudaStream_t st) {
     auto kern = c.split ? k_forward_tiny<true> : k_forward_tiny<false>;
-    // Eight CTAs per SM (64 registers, 128 threads, 32 tensor-memory
-    // columns, under 26 KB of shared memory each); carve out just their
-    // shared memory so the rest stays L1 for the grid gathers.
-    int per_sm = 8;
-    while (per_sm > 1 && (size_t)per_sm * (smem + 1024) > 227 * 1024) --per_sm;
+    const uint32_t grid_bytes = (uint32_t)c.base.level_res[0] * c.base.level_res[0] * c.base.level_res[0] * 8u;
+    const size_t smem = tiny_layout(c, grid_bytes).bytes;
+    // One CTA per SM (kGroups x 128 threads at 64 registers); carve out just
+    // its shared memory so the rest stays L1.
     static std::atomic<uint64_t> attrs_s{~0ull}, attrs_p{~0ull};
-    cudaError_t e = set_smem_attrs(kern, smem, carveout_percent((size_t)per_sm * (smem + 1024)),
-                                   c.split ? attrs_s : attrs_p);
+    cudaError_t e = set_smem_attrs(kern, smem, carveout_percent(smem + 1024), c.split ? attrs_s : attrs_p);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -500,9 +554,11 @@ cudaError_t launch_tiny(const TcCfg& c, size_t smem, const __half* grid_h, const
     }
     qb.total_tiles = t0;
     const int64_t hint = qb.n_dev ? (max_n + kTile - 1) / kTile : t0;
-    int64_t g = (int64_t)per_sm * sms;
-    if (g > hint) g = hint < 1 ? 1 : hint;
-    kern<<<(int)g, kThreads, smem, st>>>(c, reinterpret_cast<const uint2*>(grid_h), wblob, qb, status);
+    int64_t g = (hint + kGroups - 1) / kGroups;
+    if (g > sms) g = sms;
+    if (g < 1) g = 1;
+    kern<<<(int)g, kThreads * kGroups, smem, st>>>(c, reinterpret_cast<const uint2*>(grid_h), grid_bytes, wblob, qb,
+                                                   status);
     return cudaGetLastError();
 }
 
