@@ -369,12 +369,119 @@ __device__ __forceinline__ void tc_decode(const TcCfg& tc, const float (&raw)[4 
     }
 }
 
+// Warp-per-query form of the decode, sample and density (Table 1, Sec. 5.3,
+// Eq. 4): lane l of a warp owns lobe l mod KMAX of one query, so a warp
+// serves 32 / KMAX queries per pass and KMAX passes cover its 32 rows. The
+// raw outputs of the tile are staged in shared memory (row stride 4 KMAX + 4
+// floats keeps both the row writes and the lobe reads free of bank
+// conflicts). Softmax and density are reductions over the query's lanes;
+// the lobe choice takes the running sum of the weights in lobe order (a
+// serial scan, the same rounding as the thread-per-row form) and a ballot;
+// every lane samples its own lobe and the chosen lane's direction is
+// broadcast. Measured against tc_decode (one thread per query).
+template <int KMAX>
+__device__ __forceinline__ void tc_decode_warp(const TcCfg& tc, const float* __restrict__ sRaw, int warp, int lane,
+                                               int64_t j0, int64_t n, int64_t ld, const float* __restrict__ uin,
+                                               float ufrac, bool sample, float* __restrict__ dir_out,
+                                               float* __restrict__ pdf_out, float* __restrict__ mix_out,
+                                               bool log_pdf) {
+    constexpr int RS = 4 * KMAX + 4;
+    constexpr int QP = 32 / KMAX;  // queries per pass
+    constexpr unsigned kAll = 0xffffffffu;
+    const DevCfg& cfg = tc.base;
+    const int K = cfg.K;
+    const int i = lane & (KMAX - 1);
+    const int qsub = lane / KMAX;
+    const unsigned seg = KMAX == 32 ? kAll : (((1u << KMAX) - 1u) << (qsub * KMAX));
+    const bool act = i < K;
+#pragma unroll 1
+    for (int p = 0; p < KMAX; ++p) {
+        const int r = warp * 32 + p * QP + qsub;
+        const int64_t j = j0 + r;
+        const bool valid = j < n;
+        const float4 rv = *reinterpret_cast<const float4*>(sRaw + r * RS + 4 * i);
+        float mx = act ? rv.x : -INFINITY;
+#pragma unroll
+        for (int o = 1; o < KMAX; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(kAll, mx, o));
+        const float e = act ? __expf(rv.x - mx) : 0.0f;
+        float ssum = e;
+#pragma unroll
+        for (int o = 1; o < KMAX; o <<= 1) ssum += __shfl_xor_sync(kAll, ssum, o);
+        Lobe L;
+        L.lam = e * __fdividef(1.0f, ssum);
+        float th, ph;
+        decode_lobe_fast(cfg.kappa_act, rv.y, rv.z, rv.w, L, &th, &ph);
+        const float cn = vmf_scaled_norm_fast(L.kap);
+        if (mix_out && valid && act) {
+            mix_out[(4 * i + 0) * ld + j] = L.lam;
+            mix_out[(4 * i + 1) * ld + j] = L.kap;
+            mix_out[(4 * i + 2) * ld + j] = th;
+            mix_out[(4 * i + 3) * ld + j] = ph;
+        }
+        float w[3] = {0.0f, 0.0f, 1.0f};
+        bool uni = false;
+        if (sample) {
+            float u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
+            if (valid) {
+                u0 = uin[j];
+                u1 = uin[ld + j];
+                u2 = uin[2 * ld + j];
+                uni = ufrac > 0.0f && uin[3 * ld + j] < ufrac;
+            }
+            // Running sum of the weights in lobe order.
+            float cum = i == 0 ? L.lam : 0.0f;
+#pragma unroll
+            for (int k = 1; k < KMAX; ++k) {
+                const float prev = __shfl_up_sync(kAll, cum, 1);
+                if (i == k) cum = prev + L.lam;
+            }
+            const unsigned hit = __ballot_sync(kAll, act && u0 < cum) & seg;
+            const int sel = hit ? __ffs(hit) - 1 - qsub * KMAX : K - 1;
+            float d[3];
+            if (uni) uniform_sphere(u1, u2, d);
+            else vmf_sample_rp(L, u1, u2, d);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) w[a] = __shfl_sync(kAll, d[a], qsub * KMAX + sel);
+        } else if (valid) {
+            w[0] = uin[j];
+            w[1] = uin[ld + j];
+            w[2] = uin[2 * ld + j];
+        }
+        float pv;
+        if (!sample && log_pdf) {
+            const float dd = L.mu[0] * w[0] + L.mu[1] * w[1] + L.mu[2] * w[2];
+            const float a = act ? (rv.x - mx) - __logf(ssum) + __logf(cn) + L.kap * (dd - 1.0f) : -INFINITY;
+            float m = a;
+#pragma unroll
+            for (int o = 1; o < KMAX; o <<= 1) m = fmaxf(m, __shfl_xor_sync(kAll, m, o));
+            float sx = act ? __expf(a - m) : 0.0f;
+#pragma unroll
+            for (int o = 1; o < KMAX; o <<= 1) sx += __shfl_xor_sync(kAll, sx, o);
+            pv = m + __logf(sx);
+        } else {
+            pv = act ? L.lam * vmf_eval_fast(L, cn, w[0], w[1], w[2]) : 0.0f;
+#pragma unroll
+            for (int o = 1; o < KMAX; o <<= 1) pv += __shfl_xor_sync(kAll, pv, o);
+            if (sample && ufrac > 0.0f) pv = ufrac * kInv4Pi + (1.0f - ufrac) * pv;
+        }
+        if (valid && i == 0) {
+            if (sample) {
+                dir_out[j] = w[0];
+                dir_out[ld + j] = w[1];
+                dir_out[2 * ld + j] = w[2];
+            }
+            pdf_out[j] = pv;
+        }
+    }
+}
+
 // --------------------------------------------------------------- kernel
 
 // NL > 0: the network has exactly NL layers and KMAX lobes (loops over
 // layers, output chunks and lobes unrolled at compile time); NL = 0: any
-// layer count and K <= KMAX.
-template <int KMAX, bool F2, int NL>
+// layer count and K <= KMAX. WARPDEC: the warp-per-query decode
+// (tc_decode_warp) instead of one thread per query.
+template <int KMAX, bool F2, int NL, bool WARPDEC = false>
 __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 6) : (KMAX == 8 ? 3 : 1)) k_forward_tc(const __grid_constant__ TcCfg tc,
                                                          const __half* __restrict__ grid_h,
                                                          const uint8_t* __restrict__ wblob,
@@ -542,13 +649,31 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 
             }
         }
         if (!ok) break;
-        float rawf[4 * KMAX];
+        if constexpr (WARPDEC) {
+            // Stage the raw outputs in the activation buffer (free until the
+            // next tile's encode), then decode a query per 32 / KMAX lanes.
+            constexpr int RS = 4 * KMAX + 4;
+            float* sRaw = reinterpret_cast<float*>(sA);
 #pragma unroll
-        for (int c = 0; c < 4 * KMAX / 16; ++c)
+            for (int c = 0; c < 4 * KMAX / 16; ++c)
+                if (c * 16 < tc.layer[L - 1].Np)
 #pragma unroll
-            for (int i = 0; i < 16; ++i) rawf[c * 16 + i] = __uint_as_float(raw[c][i]);
-        tc_decode<KMAX, (NL > 0)>(tc, rawf, j, valid, ld, S.uin, S.ufrac, qb.sample != 0, S.dir, S.pdf, S.mix,
-                                  qb.log_pdf != 0);
+                    for (int q = 0; q < 4; ++q)
+                        *reinterpret_cast<uint4*>(sRaw + t * RS + 16 * c + 4 * q) =
+                            make_uint4(raw[c][4 * q], raw[c][4 * q + 1], raw[c][4 * q + 2], raw[c][4 * q + 3]);
+            __syncthreads();
+            tc_decode_warp<KMAX>(tc, sRaw, warp, t & 31, (tile - S.tile0) * kTile, n, ld, S.uin, S.ufrac,
+                                 qb.sample != 0, S.dir, S.pdf, S.mix, qb.log_pdf != 0);
+            __syncthreads();
+        } else {
+            float rawf[4 * KMAX];
+#pragma unroll
+            for (int c = 0; c < 4 * KMAX / 16; ++c)
+#pragma unroll
+                for (int i = 0; i < 16; ++i) rawf[c * 16 + i] = __uint_as_float(raw[c][i]);
+            tc_decode<KMAX, (NL > 0)>(tc, rawf, j, valid, ld, S.uin, S.ufrac, qb.sample != 0, S.dir, S.pdf, S.mix,
+                                      qb.log_pdf != 0);
+        }
     }
     if (!ok) {
         if (t == 0) atomicOr(status, kStatusTimeout);
@@ -1313,10 +1438,10 @@ cudaError_t tc_refresh_weights(npm_handle* h, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int KMAX, bool F2, int NL>
+template <int KMAX, bool F2, int NL, bool WARPDEC = false>
 static cudaError_t launch_tc(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStream_t st) {
     TcState* s = h->tc;
-    auto kern = k_forward_tc<KMAX, F2, NL>;
+    auto kern = k_forward_tc<KMAX, F2, NL, WARPDEC>;
     // CTAs per SM from registers (the instance's count, queried once) and
     // tensor memory; then carve out just the shared memory they need so the
     // rest stays L1 for the grid gathers.
@@ -1430,6 +1555,20 @@ cudaError_t tc_query_batch(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStr
     if (tiny_qualifies(h->tc->cfg) && env_override("NPM_TC_TINY", env_tiny) != 0) {
         const uint8_t* wb = h->ema ? h->tc->wblob_inf : h->tc->wblob;
         return launch_tiny(h->tc->cfg, h->tc->smem, h->grid_h, wb, qb, max_n, reinterpret_cast<int*>(h->scalars + 8), st);
+    }
+    // Tuning override NPM_TC_DECODE=1: the warp-per-query decode in the
+    // general kernel (built for the four- and eight-lobe instances; it stages
+    // the raw outputs in the activation buffers, which must hold them).
+    static std::atomic<int> env_dec{INT32_MIN + 1};
+    const TcCfg& c = h->tc->cfg;
+    const int kmax = K <= 4 ? 4 : 8;
+    const bool fits = (size_t)(c.split ? 2 : 1) * c.a_bytes >= (size_t)kTile * (16 * kmax + 16);
+    if (env_override("NPM_TC_DECODE", env_dec) == 1 && K <= 8 && fits) {
+        if (K <= 4) {
+            if (L == 3 && K == 4 && !f2) return launch_tc<4, false, 3, true>(h, qb, max_n, st);
+            return f2 ? launch_tc<4, true, 0, true>(h, qb, max_n, st) : launch_tc<4, false, 0, true>(h, qb, max_n, st);
+        }
+        return f2 ? launch_tc<8, true, 0, true>(h, qb, max_n, st) : launch_tc<8, false, 0, true>(h, qb, max_n, st);
     }
     // The small three-layer four-lobe networks get an instance with the layer
     // and lobe loops unrolled (measured faster there; on the four-layer

@@ -341,10 +341,13 @@ __global__ void __launch_bounds__(kThreads * kGroups, 1) k_forward_tiny(const __
                 z = S.pos[2 * ld + j];
             }
             const Cell cl = make_cell(x, y, z, D);
-            const uint32_t b = cl.c[0] + uD * (cl.c[1] + uD * cl.c[2]);
+            // Corners (x, x + 1) are adjacent entries: four row addresses,
+            // the x-neighbour one entry on.
+            const uint2* r00 = sG + (cl.c[0] + uD * (cl.c[1] + uD * cl.c[2]));
+            const uint2* rows[4] = {r00, r00 + uD, r00 + uD2, r00 + uD2 + uD};
             uint2 raw[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) raw[c] = sG[b + (c & 1) + ((c & 2) ? uD : 0u) + ((c & 4) ? uD2 : 0u)];
+            for (int c = 0; c < 8; ++c) raw[c] = rows[c >> 1][c & 1];
             float w8[8];
             corner_w8(cl, w8);
             float2 a01 = make_float2(0.0f, 0.0f), a23 = make_float2(0.0f, 0.0f);
@@ -374,15 +377,20 @@ __global__ void __launch_bounds__(kThreads * kGroups, 1) k_forward_tiny(const __
             const TcLayer& ly = tc.layer[l];
             if (t == 0) {
                 tc_fence_after();
-                const uint32_t sbo = (uint32_t)(ly.Kp >> 3) * 128u;
-                const uint32_t a_addr = smem_u32(sA), w_addr = smem_u32(sW) + ly.w_off;
-                for (int s = 0; s < (ly.Kp >> 4); ++s) {
-                    const uint64_t ad = umma_desc(a_addr + s * 256u, 128u, sbo);
-                    const uint64_t bd = umma_desc(w_addr + s * 256u, 128u, sbo);
-                    mma_bf16(tmem, ad, bd, ly.idesc, s > 0 ? 1u : 0u);
-                    if (SPLIT) {
-                        mma_bf16(tmem, ad, umma_desc(w_addr + tc.w_bytes + s * 256u, 128u, sbo), ly.idesc, 1u);
-                        mma_bf16(tmem, umma_desc(a_addr + lo_off + s * 256u, 128u, sbo), bd, ly.idesc, 1u);
+                // Descriptors of K step s are those of step 0 with the start
+                // address 256 bytes (16 units) further.
+                const uint64_t ad = umma_desc(smem_u32(sA), 128u, (uint32_t)(ly.Kp >> 3) * 128u);
+                const uint64_t bd = umma_desc(smem_u32(sW) + ly.w_off, 128u, (uint32_t)(ly.Kp >> 3) * 128u);
+                const uint64_t bl = bd + (uint64_t)(tc.w_bytes >> 4), al = ad + (uint64_t)(lo_off >> 4);
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    if (s < (ly.Kp >> 4)) {
+                        const uint64_t o = (uint64_t)(16 * s);
+                        mma_bf16(tmem, ad + o, bd + o, ly.idesc, s > 0 ? 1u : 0u);
+                        if (SPLIT) {
+                            mma_bf16(tmem, ad + o, bl + o, ly.idesc, 1u);
+                            mma_bf16(tmem, al + o, bd + o, ly.idesc, 1u);
+                        }
                     }
                 }
                 mma_commit(bar_mma);

@@ -154,6 +154,9 @@ WORKLOADS = {
     "tiny_bf16": TINY_BF16,
     "product_bf16": PRODUCT_BF16,
     "paper_own": PAPER_OWN,
+    "paper_hash_bf16": PAPER_HASH.with_(
+        name="hash grid 16 levels x 2 feats, T=2^19, MLP 32-64-64-64-32, K=8, split-bf16",
+        precision=BF16X3),
     "paper_own_bf16": PAPER_OWN.with_(
         name="paper's own shape: 8 dense levels D 8..86 x 4 feats, MLP 32-64-64-64-32, K=8, split-bf16",
         precision=BF16X3),
