@@ -555,17 +555,16 @@ static npm_status adam_impl(npm_handle* h, const float* loss, cudaStream_t st) {
     int* status = reinterpret_cast<int*>(h->scalars + 8);
     NPM_CUDA(npm::launch_adam(h->n_int, h->params, h->grads, h->adam_m, h->adam_v, h->cfg.lr,
                               h->cfg.beta1, h->cfg.beta2, h->cfg.eps, step_dev(h), loss, status,
-                              h->grid_h, h->grid_h ? (h->ng / 4) * 4 : 0, h->ema, h->ema_decay, st),
+                              h->grid_h, h->grid_h ? h->ng : 0, h->ema, h->ema_decay, st),
              "adam launch");
-    if (h->grid_h && h->ng % 4) {
-        // The last ng % 4 entries, beyond the Adam kernel's float4 lanes.
-        const int64_t b = (h->ng / 4) * 4;
-        NPM_CUDA(npm::launch_to_half(h->ng - b, inf_params(h) + b, h->grid_h + b, st), "grid fp16 tail");
+    // The FP32 kernels' padded weights: needed unless the tensor-core
+    // kernels serve both inference and training.
+    if (!(h->tc && npm::tc_can_train(h))) {
+        NPM_CUDA(npm::launch_arrange_weights(h->dc, h->params + h->mlp_off, h->wfwd, h->wbwd, st),
+                 "arrange weights");
+        npm_status s = arrange_inference_weights(h, st);
+        if (s != NPM_OK) return s;
     }
-    NPM_CUDA(npm::launch_arrange_weights(h->dc, h->params + h->mlp_off, h->wfwd, h->wbwd, st),
-             "arrange weights");
-    npm_status s = arrange_inference_weights(h, st);
-    if (s != NPM_OK) return s;
     if (h->tc) NPM_CUDA(npm::tc_refresh_weights(h, st), "bf16 weight copy");
     return NPM_OK;
 }

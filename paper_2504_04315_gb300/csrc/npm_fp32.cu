@@ -1027,7 +1027,7 @@ __global__ void k_arrange_weights(DevCfg cfg, const float* __restrict__ mlp,
 __global__ void k_adam(int64_t n4, float4* __restrict__ p, float4* __restrict__ g,
                        float4* __restrict__ m, float4* __restrict__ v, float lr, float b1, float b2,
                        float eps, const int* __restrict__ steps, const float* __restrict__ loss,
-                       int* __restrict__ status, __half2* __restrict__ half_copy, int64_t n_half4,
+                       int* __restrict__ status, __half2* __restrict__ half_copy, int64_t n_half,
                        float4* __restrict__ ema, float ema_decay) {
     const bool skip = loss != nullptr && !isfinite(*loss);
     if (skip && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatusNumeric);
@@ -1080,9 +1080,16 @@ __global__ void k_adam(int64_t n4, float4* __restrict__ p, float4* __restrict__ 
                 ema[i] = e;
                 inf = e;
             }
-            if (half_copy && i < n_half4) {
-                half_copy[2 * i] = __floats2half2_rn(inf.x, inf.y);
-                half_copy[2 * i + 1] = __floats2half2_rn(inf.z, inf.w);
+            if (half_copy && 4 * i < n_half) {
+                if (4 * i + 4 <= n_half) {
+                    half_copy[2 * i] = __floats2half2_rn(inf.x, inf.y);
+                    half_copy[2 * i + 1] = __floats2half2_rn(inf.z, inf.w);
+                } else {
+                    // The copy's last entries (n_half not a multiple of 4).
+                    __half* hc = reinterpret_cast<__half*>(half_copy) + 4 * i;
+                    const float iv[4] = {inf.x, inf.y, inf.z, inf.w};
+                    for (int c = 0; c < (int)(n_half - 4 * i); ++c) hc[c] = __float2half_rn(iv[c]);
+                }
             }
         }
     }
@@ -1323,7 +1330,7 @@ cudaError_t launch_adam(int64_t n, float* p, float* g, float* m, float* v, float
     k_adam<<<grid, 256, 0, st>>>(n4, reinterpret_cast<float4*>(p), reinterpret_cast<float4*>(g),
                                  reinterpret_cast<float4*>(m), reinterpret_cast<float4*>(v), lr, b1,
                                  b2, eps, steps, loss, status,
-                                 reinterpret_cast<__half2*>(half_copy), n_half / 4,
+                                 reinterpret_cast<__half2*>(half_copy), n_half,
                                  reinterpret_cast<float4*>(ema), ema_decay);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
