@@ -943,7 +943,7 @@ __global__ void __launch_bounds__(kTrainThreads, train_ctas_per_sm(KMAX, F2)) k_
     const uint8_t* __restrict__ wblob, int64_t n, int64_t ld, const float* __restrict__ pos,
     const float* __restrict__ aux, const float* __restrict__ dir, const float* __restrict__ rad,
     const float* __restrict__ spdf, const float* __restrict__ dlogv, float inv_n, float* __restrict__ grad,
-    int64_t mlp_off, float* __restrict__ loss, int* __restrict__ status, const float* __restrict__ enc, int prefetch) {
+    int64_t mlp_off, float* __restrict__ loss, int* __restrict__ status, const float* __restrict__ enc) {
     extern __shared__ __align__(1024) uint8_t smem[];
     constexpr int KH = KMAX / 2;
     uint8_t* sW = smem;
@@ -1020,74 +1020,10 @@ __global__ void __launch_bounds__(kTrainThreads, train_ctas_per_sm(KMAX, F2)) k_
         }
     };
     const int64_t ntiles = (n + kTile - 1) / kTile;
-    // Gather of the next tile's grid features (2-feature grids, prefetch
-    // mode): this half's levels [lv0, lv1), one level per MMA wait of the
-    // current tile, so that the random L2 reads overlap the tensor-core work;
-    // nf holds the features in level order once all are gathered.
-    float nf[16];
-    float nx = 0.0f, ny = 0.0f, nz = 0.0f;
-    bool gpend = false;
-    int gq = 0;
-    auto gather_next = [&]() {
-        if (F2 && gpend && gq < 8) {
-            const int l = lv0 + gq;
-            float a0 = 0.0f, a1 = 0.0f;
-            if (l < lv1) {
-                const Cell cl = make_cell(nx, ny, nz, cfg.level_res[l]);
-                const float* gr = grid32 + (size_t)cfg.level_off[l] * 2;
-                float2 v[8];
-#pragma unroll
-                for (int c = 0; c < 8; c += 2)
-                    gather_pair2(gr, cfg.level_off[l], corner_idx1(cfg, l, cl, c), corner_idx1(cfg, l, cl, c + 1), v[c],
-                                 v[c + 1]);
-                float ws[8];
-                corner_w8(cl, ws);
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    a0 = fmaf(ws[c], v[c].x, a0);
-                    a1 = fmaf(ws[c], v[c].y, a1);
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < 14; ++i) nf[i] = nf[i + 2];
-            nf[14] = a0;
-            nf[15] = a1;
-            ++gq;
-        }
-    };
-    auto gather_setup = [&](int64_t tl) {
-        gpend = F2 && prefetch && tl < ntiles;
-        gq = 0;
-        if (gpend) {
-            const int64_t jn = tl * kTile + row;
-            const bool vn = jn < n;
-            nx = vn ? pos[jn] : 0.0f;
-            ny = vn ? pos[ld + jn] : 0.0f;
-            nz = vn ? pos[2 * ld + jn] : 0.0f;
-        }
-    };
-    // The CTA's first tile is gathered before the loop.
-    gather_setup(blockIdx.x);
-    while (gpend && gq < 8) gather_next();
     for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
         const int64_t j = tile * kTile + row;
         const bool valid = j < n;
-        if (F2 && prefetch) {
-            // This half's prefetched grid features (levels lv0 .. lv1), then
-            // the product-mode inputs and the padding; the next tile's
-            // gather starts.
-            while (gpend && gq < 8) gather_next();  // networks with fewer than 4 layers
-            const int kp0 = tc.layer[0].Kp;
-            const uint32_t lo = tc.split ? tc.a_bytes : 0u;
-            const int nlv = lv1 - lv0;
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (q < nlv) store_pair(smem + tt.h_off[0], tile_off(row, 2 * (lv0 + q), kp0), valid ? nf[2 * q] : 0.0f,
-                                        valid ? nf[2 * q + 1] : 0.0f, lo);
-            tc_encode<F2>(tc, grid32, j, valid, ld, pos, aux, smem + tt.h_off[0], row, lo, true, lv1, lv1,
-                          half == 1);
-            gather_setup(tile + gridDim.x);
-        } else if (F2 && enc) {
+        if (F2 && enc) {
             // This half's grid features from k_train_encode (two per level),
             // then the product-mode inputs and the padding.
             const int kp0 = tc.layer[0].Kp;
@@ -1125,7 +1061,6 @@ __global__ void __launch_bounds__(kTrainThreads, train_ctas_per_sm(KMAX, F2)) k_
                 mma_commit(bar_mma);
             }
             scatter_next();  // the previous tile's grid gradient, one level
-            gather_next();   // the next tile's grid features, one level
             // Warp 0 spins on the barrier; the others sleep at the CTA
             // barrier, which then orders their TMEM reads after completion.
             const bool done = warp != 0 || mbar_wait_bounded(bar_mma, phase);
@@ -1222,7 +1157,6 @@ __global__ void __launch_bounds__(kTrainThreads, train_ctas_per_sm(KMAX, F2)) k_
                 mma_commit(bar_mma);
             }
             scatter_next();
-            gather_next();
             const bool done = warp != 0 || mbar_wait_bounded(bar_mma, phase);
             phase ^= 1u;
             ok = !__syncthreads_or(!done);
@@ -1575,13 +1509,7 @@ static cudaError_t launch_train_tc(npm_handle* h, int64_t n, int64_t ld, const f
     const int g = (int)(ntiles < slots ? ntiles : slots);
     int* status = reinterpret_cast<int*>(h->scalars + 8);
     const float* enc = nullptr;
-    // 2-feature grids: the training kernel gathers each next tile's grid
-    // features during the current tile's MMA waits (prefetch), or reads them
-    // from a workspace that k_train_encode fills first; tuning override
-    // NPM_TRAIN_PREFETCH=0 selects the encode kernel.
-    static std::atomic<int> env_pf{INT32_MIN + 1};
-    const int prefetch = F2 && env_override("NPM_TRAIN_PREFETCH", env_pf) != 0 ? 1 : 0;
-    if (F2 && !prefetch && s->enc && n <= h->cfg.max_batch) {
+    if (F2 && s->enc && n <= h->cfg.max_batch) {
         // Levels per thread: two (64 registers, more warps) measured a little
         // faster than four; tuning override NPM_ENC_LPT (2 or 4).
         static std::atomic<int> env_lpt{INT32_MIN + 1};
@@ -1598,7 +1526,7 @@ static cudaError_t launch_train_tc(npm_handle* h, int64_t n, int64_t ld, const f
     const uint8_t* wb = s->wblob_train ? s->wblob_train : s->wblob;
     kern<<<g < 1 ? 1 : g, kTrainThreads, s->train.smem, st>>>(s->train_cfg, s->train, h->params, wb, n, ld, pos,
                                                          aux, dir, rad, spdf, dlogv, 1.0f / (float)n, h->grads,
-                                                         h->mlp_off, loss, status, enc, prefetch);
+                                                         h->mlp_off, loss, status, enc);
     return cudaGetLastError();
 }
 
