@@ -36,6 +36,14 @@
  *   - Positions outside [0,1]^3 are clamped to the box; direction arguments
  *     are unit vectors.
  *   - npm_last_error() returns a thread-local description of the last error.
+ *   - Each entry point opens an NVTX range named after itself, so profiler
+ *     timelines group the kernels of each call.
+ *   - Test-only fault injection (host side; off unless set in the
+ *     environment): NPM_TEST_FAIL_ALLOC=N fails the N-th device allocation
+ *     of each npm_create with NPM_ERR_OOM (everything allocated before is
+ *     freed); NPM_TEST_FAIL_LAUNCH=N makes the N-th hot call of the process
+ *     (query, evaluation, training or backward) return NPM_ERR_CUDA as if
+ *     its launch had failed, launching nothing.
  *   - A handle may be used from one host thread at a time.
  */
 #ifndef NPM_H
@@ -496,6 +504,15 @@ npm_status npm_pdf_integral(npm_handle* h, int64_t n_pos, const float* pos, cons
  * tensor-core kernels keep their fixed bound. Errors: NPM_ERR_INVALID_ARG
  * (NULL handle). */
 npm_status npm_set_wait_limit(npm_handle* h, int64_t cycles);
+
+/* Debug builds (compiled with NPM_DEBUG_BOUNDS; not a hot call): every
+ * kernel checks each grid-entry index and queue slot it computes against
+ * its buffer before the access; an index out of range is counted and
+ * replaced by 0 (the kernel carries on; no trap). Returns the count since
+ * the library was loaded on the current device, -1 in a normal build
+ * (checks compiled out), -2 if the count cannot be read. Synchronises
+ * with the device. The paper has no counterpart. */
+int64_t npm_debug_bounds_violations(void);
 
 /* Thread-local text of the last error returned on this thread. */
 const char* npm_last_error(void);

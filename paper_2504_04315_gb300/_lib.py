@@ -84,6 +84,7 @@ SIGNATURES = {
     "npm_query_sample_host": (st, [vp, i64, vp, vp, vp, i64, f32, vp, vp, vp]),
     "npm_eval_pdf": (st, [vp, i64, vp, vp, vp, i64, vp, vp]),
     "npm_eval_log_pdf": (st, [vp, i64, vp, vp, vp, i64, vp, vp]),
+    "npm_debug_bounds_violations": (i64, []),
     "npm_train_step": (st, [vp, i64, vp, vp, vp, vp, vp, i64, vp, vp]),
     "npm_backward": (st, [vp, i64, vp, vp, vp, vp, i64, vp]),
     "npm_adam_step": (st, [vp, vp]),
@@ -130,11 +131,14 @@ def load():
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB):
+    # NPM_LIBRARY selects another in-tree build (the bounds-checking debug
+    # build of _build.build_debug()).
+    path = os.environ.get("NPM_LIBRARY") or LIB
+    if not os.path.exists(path):
         raise RuntimeError(
-            "libnpm_gb300.so is not built; run paper_2504_04315_gb300._build.build() "
+            f"{path} is not built; run paper_2504_04315_gb300._build.build() "
             "(or __graft_entry__.build()). There is no CPU fallback.")
-    lib = C.CDLL(LIB)
+    lib = C.CDLL(path)
     for name, (res, args) in SIGNATURES.items():
         fn = getattr(lib, name)
         fn.restype = res

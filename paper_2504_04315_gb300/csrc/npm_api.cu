@@ -4,12 +4,53 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <stdlib.h>
+
+#include <atomic>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "npm.h"
 #include "npm_handle.h"
 #include "npm_kernels.h"
+
+namespace npm {
+
+#ifdef NPM_DEBUG_BOUNDS
+__device__ unsigned long long g_bounds_violations = 0;
+#endif
+
+CallRange::CallRange(const char* name) { nvtxRangePushA(name); }
+CallRange::~CallRange() { nvtxRangePop(); }
+
+namespace {
+thread_local int t_alloc_count = 0;  // allocations of the current npm_create
+thread_local int t_alloc_fail = 0;   // which one fails (0: none)
+std::atomic<long long> g_launch_count{0};
+}  // namespace
+
+cudaError_t device_alloc(void** p, size_t bytes) {
+    if (t_alloc_fail > 0 && ++t_alloc_count == t_alloc_fail) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+bool inject_launch_failure() {
+    static std::atomic<long long> target{-2};
+    long long t = target.load(std::memory_order_relaxed);
+    if (t == -2) {
+        const char* e = getenv("NPM_TEST_FAIL_LAUNCH");
+        t = (e && *e) ? atoll(e) : 0;
+        target.store(t, std::memory_order_relaxed);
+    }
+    return t > 0 && g_launch_count.fetch_add(1, std::memory_order_relaxed) + 1 == t;
+}
+
+}  // namespace npm
 
 namespace {
 
@@ -87,7 +128,7 @@ template <typename T>
 npm_status dalloc(T** p, size_t count, const char* what) {
     *p = nullptr;
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    cudaError_t e = npm::device_alloc((void**)p, count * sizeof(T));
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -196,8 +237,19 @@ extern "C" {
 const char* npm_last_error(void) { return g_last_error.c_str(); }
 
 npm_status npm_create(const npm_config* cfg, npm_handle** out) {
+    npm::CallRange range("npm_create");
     if (!out) return fail(NPM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
+    // Test-only: NPM_TEST_FAIL_ALLOC=N fails the N-th allocation of this
+    // call; the guard switches the injection off again on every return.
+    struct AllocInjection {
+        AllocInjection() {
+            const char* e = getenv("NPM_TEST_FAIL_ALLOC");
+            npm::t_alloc_fail = (e && *e) ? atoi(e) : 0;
+            npm::t_alloc_count = 0;
+        }
+        ~AllocInjection() { npm::t_alloc_fail = 0; }
+    } injection;
     npm_status s = validate(cfg);
     if (s != NPM_OK) return s;
     npm_handle* h = new npm_handle();
@@ -282,6 +334,7 @@ npm_status npm_create(const npm_config* cfg, npm_handle** out) {
 }
 
 npm_status npm_destroy(npm_handle* h) {
+    npm::CallRange range("npm_destroy");
     if (!h) return NPM_OK;
     cudaDeviceSynchronize();
     if (h->tc) npm::tc_destroy(h);
@@ -318,6 +371,7 @@ static npm_status copy_public(npm_handle* h, float* dev, float* host, int64_t co
 }
 
 npm_status npm_set_params(npm_handle* h, const float* host, int64_t count) {
+    npm::CallRange range("npm_set_params");
     npm_status s = copy_public(h, h ? h->params : nullptr, const_cast<float*>(host), count, true);
     if (s != NPM_OK) return s;
     if (h->ema)  // the average restarts from the new parameters
@@ -329,10 +383,12 @@ npm_status npm_set_params(npm_handle* h, const float* host, int64_t count) {
 }
 
 npm_status npm_get_params(npm_handle* h, float* host, int64_t count) {
+    npm::CallRange range("npm_get_params");
     return copy_public(h, h ? h->params : nullptr, host, count, false);
 }
 
 npm_status npm_set_params_device(npm_handle* h, const float* dev, int64_t count, void* stream) {
+    npm::CallRange range("npm_set_params_device");
     if (!h || !dev) return fail(NPM_ERR_INVALID_ARG, "NULL argument");
     if (count != h->ng + h->nmlp) return fail(NPM_ERR_INVALID_ARG, "count != npm_num_params");
     cudaStream_t st = (cudaStream_t)stream;
@@ -347,6 +403,7 @@ npm_status npm_set_params_device(npm_handle* h, const float* dev, int64_t count,
 }
 
 npm_status npm_get_grads_device(npm_handle* h, float* dev, int64_t count, void* stream) {
+    npm::CallRange range("npm_get_grads_device");
     if (!h || !dev) return fail(NPM_ERR_INVALID_ARG, "NULL argument");
     if (count != h->ng + h->nmlp) return fail(NPM_ERR_INVALID_ARG, "count != npm_num_params");
     cudaStream_t st = (cudaStream_t)stream;
@@ -358,6 +415,7 @@ npm_status npm_get_grads_device(npm_handle* h, float* dev, int64_t count, void* 
 }
 
 npm_status npm_set_ema(npm_handle* h, float decay, void* stream) {
+    npm::CallRange range("npm_set_ema");
     if (!h) return fail(NPM_ERR_INVALID_ARG, "handle is NULL");
     if (!(decay >= 0.0f && decay < 1.0f)) return fail(NPM_ERR_INVALID_ARG, "decay must be in [0, 1)");
     cudaStream_t st = (cudaStream_t)stream;
@@ -429,8 +487,10 @@ npm_status npm_set_adam(npm_handle* h, int step, const float* m_host, const floa
 npm_status npm_query_sample(npm_handle* h, int64_t n, const float* pos, const float* aux,
                             const float* u, int64_t ld, float uniform_frac, float* dir_out,
                             float* pdf_out, float* mix_out, void* stream) {
+    npm::CallRange range("npm_query_sample");
     npm_status s = check_call(h, n, ld, pos, aux);
     if (s != NPM_OK) return s;
+    if (npm::inject_launch_failure()) return fail(NPM_ERR_CUDA, "injected launch failure (test)");
     if (!(uniform_frac >= 0.0f && uniform_frac <= 1.0f))
         return fail(NPM_ERR_INVALID_ARG, "uniform_frac outside [0, 1]");
     if (n > 0 && (!u || !dir_out || !pdf_out))
@@ -447,8 +507,10 @@ npm_status npm_query_sample(npm_handle* h, int64_t n, const float* pos, const fl
 npm_status npm_query_sample_host(npm_handle* h, int64_t n, const float* pos, const float* aux,
                                  const float* u, int64_t ld, float uniform_frac, float* dir_out,
                                  float* pdf_out, void* stream) {
+    npm::CallRange range("npm_query_sample_host");
     npm_status s = check_call(h, n, ld, pos, aux);
     if (s != NPM_OK) return s;
+    if (npm::inject_launch_failure()) return fail(NPM_ERR_CUDA, "injected launch failure (test)");
     if (!(uniform_frac >= 0.0f && uniform_frac <= 1.0f))
         return fail(NPM_ERR_INVALID_ARG, "uniform_frac outside [0, 1]");
     if (n > 0 && (!u || !dir_out || !pdf_out))
@@ -505,8 +567,10 @@ npm_status npm_query_sample_host(npm_handle* h, int64_t n, const float* pos, con
 
 npm_status npm_eval_pdf(npm_handle* h, int64_t n, const float* pos, const float* aux,
                         const float* dir, int64_t ld, float* pdf_out, void* stream) {
+    npm::CallRange range("npm_eval_pdf");
     npm_status s = check_call(h, n, ld, pos, aux);
     if (s != NPM_OK) return s;
+    if (npm::inject_launch_failure()) return fail(NPM_ERR_CUDA, "injected launch failure (test)");
     if (n > 0 && (!dir || !pdf_out)) return fail(NPM_ERR_INVALID_ARG, "dir and pdf_out are required");
     if (n == 0) return NPM_OK;
     cudaStream_t st = (cudaStream_t)stream;
@@ -519,8 +583,10 @@ npm_status npm_eval_pdf(npm_handle* h, int64_t n, const float* pos, const float*
 
 npm_status npm_eval_log_pdf(npm_handle* h, int64_t n, const float* pos, const float* aux,
                             const float* dir, int64_t ld, float* logpdf_out, void* stream) {
+    npm::CallRange range("npm_eval_log_pdf");
     npm_status s = check_call(h, n, ld, pos, aux);
     if (s != NPM_OK) return s;
+    if (npm::inject_launch_failure()) return fail(NPM_ERR_CUDA, "injected launch failure (test)");
     if (n > 0 && (!dir || !logpdf_out)) return fail(NPM_ERR_INVALID_ARG, "dir and logpdf_out are required");
     if (n == 0) return NPM_OK;
     cudaStream_t st = (cudaStream_t)stream;
@@ -572,8 +638,10 @@ static npm_status adam_impl(npm_handle* h, const float* loss, cudaStream_t st) {
 npm_status npm_train_step(npm_handle* h, int64_t n, const float* pos, const float* aux,
                           const float* dir, const float* radiance, const float* sample_pdf,
                           int64_t ld, float* loss_out, void* stream) {
+    npm::CallRange range("npm_train_step");
     npm_status s = check_call(h, n, ld, pos, aux);
     if (s != NPM_OK) return s;
+    if (npm::inject_launch_failure()) return fail(NPM_ERR_CUDA, "injected launch failure (test)");
     if (n > 0 && (!dir || !radiance || !sample_pdf))
         return fail(NPM_ERR_INVALID_ARG, "dir, radiance and sample_pdf are required");
     cudaStream_t st = (cudaStream_t)stream;
@@ -586,8 +654,10 @@ npm_status npm_train_step(npm_handle* h, int64_t n, const float* pos, const floa
 
 npm_status npm_backward(npm_handle* h, int64_t n, const float* pos, const float* aux,
                         const float* dir, const float* dlogv, int64_t ld, void* stream) {
+    npm::CallRange range("npm_backward");
     npm_status s = check_call(h, n, ld, pos, aux);
     if (s != NPM_OK) return s;
+    if (npm::inject_launch_failure()) return fail(NPM_ERR_CUDA, "injected launch failure (test)");
     if (n > 0 && (!dir || !dlogv)) return fail(NPM_ERR_INVALID_ARG, "dir and dlogv are required");
     cudaStream_t st = (cudaStream_t)stream;
     NPM_CUDA(cudaMemsetAsync(h->grads, 0, h->n_int * sizeof(float), st), "clear grads");
@@ -595,12 +665,14 @@ npm_status npm_backward(npm_handle* h, int64_t n, const float* pos, const float*
 }
 
 npm_status npm_adam_step(npm_handle* h, void* stream) {
+    npm::CallRange range("npm_adam_step");
     if (!h) return fail(NPM_ERR_INVALID_ARG, "handle is NULL");
     return adam_impl(h, nullptr, (cudaStream_t)stream);
 }
 
 npm_status npm_grid_indices(npm_handle* h, int64_t n, const float* pos, int64_t ld, int32_t* out,
                             void* stream) {
+    npm::CallRange range("npm_grid_indices");
     npm_status s = check_call(h, n, ld, pos, nullptr);
     if (s != NPM_OK && s != NPM_ERR_INVALID_ARG) return s;
     if (!h) return s;
@@ -613,6 +685,7 @@ npm_status npm_grid_indices(npm_handle* h, int64_t n, const float* pos, int64_t 
 }
 
 npm_status npm_check_device_status(npm_handle* h, void* stream) {
+    npm::CallRange range("npm_check_device_status");
     if (!h) return fail(NPM_ERR_INVALID_ARG, "handle is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     int word = 0;
@@ -626,6 +699,19 @@ npm_status npm_check_device_status(npm_handle* h, void* stream) {
     return NPM_OK;
 }
 
+int64_t npm_debug_bounds_violations(void) {
+#ifdef NPM_DEBUG_BOUNDS
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, npm::g_bounds_violations, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        return -2;
+    }
+    return (int64_t)v;
+#else
+    return -1;
+#endif
+}
+
 npm_status npm_set_wait_limit(npm_handle* h, int64_t cycles) {
     if (!h) return fail(NPM_ERR_INVALID_ARG, "handle is NULL");
     h->wait_limit = cycles;
@@ -637,6 +723,7 @@ npm_status npm_set_wait_limit(npm_handle* h, int64_t cycles) {
 static const char kMagic[8] = {'N', 'P', 'M', 'C', 'K', 'P', 'T', '1'};
 
 npm_status npm_save(npm_handle* h, const char* path) {
+    npm::CallRange range("npm_save");
     if (!h || !path) return fail(NPM_ERR_INVALID_ARG, "NULL argument");
     const int64_t np = h->ng + h->nmlp;
     std::vector<float> p(np), m(np), v(np);
@@ -658,6 +745,7 @@ npm_status npm_save(npm_handle* h, const char* path) {
 }
 
 npm_status npm_load(npm_handle* h, const char* path) {
+    npm::CallRange range("npm_load");
     if (!h || !path) return fail(NPM_ERR_INVALID_ARG, "NULL argument");
     FILE* f = fopen(path, "rb");
     if (!f) return fail(NPM_ERR_IO, std::string("cannot open ") + path);

@@ -39,6 +39,35 @@ struct DevCfg {
     int max_width;
 };
 
+// ------------------------------------------------------ debug bounds
+
+// With NPM_DEBUG_BOUNDS defined (a separate debug build of the library),
+// bounded_index checks a grid-entry or queue-slot index against its limit
+// before the access: an index at or beyond the limit is counted in
+// g_bounds_violations and replaced by 0, so the access stays inside the
+// buffer and the kernel carries on (no trap). npm_debug_bounds_violations
+// reads the count. In the normal build the check compiles away.
+#ifdef NPM_DEBUG_BOUNDS
+extern __device__ unsigned long long g_bounds_violations;
+__device__ __forceinline__ uint32_t bounded_index(uint32_t idx, uint32_t limit) {
+    if (idx >= limit) {
+        atomicAdd(&g_bounds_violations, 1ull);
+        return 0u;
+    }
+    return idx;
+}
+__device__ __forceinline__ int64_t bounded_slot(int64_t j, int64_t limit) {
+    if (j < 0 || j >= limit) {
+        atomicAdd(&g_bounds_violations, 1ull);
+        return 0;
+    }
+    return j;
+}
+#else
+__device__ __forceinline__ uint32_t bounded_index(uint32_t idx, uint32_t) { return idx; }
+__device__ __forceinline__ int64_t bounded_slot(int64_t j, int64_t) { return j; }
+#endif
+
 // ------------------------------------------------------ lattice (Eq. 11)
 
 // Cell and fraction along one axis: x clamped to [0,1] (NaN -> 0),
@@ -82,7 +111,8 @@ __device__ __forceinline__ void corner_idx8(const DevCfg& cfg, int l, const Cell
         const uint32_t b = cl.c[0] + D * (cl.c[1] + D * cl.c[2]);
         const uint32_t dy = D, dz = D * D;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) idx[c] = b + (c & 1) + ((c & 2) ? dy : 0u) + ((c & 4) ? dz : 0u);
+        for (int c = 0; c < 8; ++c)
+            idx[c] = bounded_index(b + (c & 1) + ((c & 2) ? dy : 0u) + ((c & 4) ? dz : 0u), D * D * D);
     } else {
         const uint32_t hx[2] = {cl.c[0], cl.c[0] + 1u};
         const uint32_t hy0 = cl.c[1] * 2654435761u, hz0 = cl.c[2] * 805459861u;

@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kAdvanceThreads) k_wf_advance(WfState s, int b
         }
         __syncthreads();
         if (keep) {
-            const int64_t j = (int64_t)s_base + s_off[warp] + __popc(mask & ((1u << lane) - 1u));
+            const int64_t j = npm::bounded_slot((int64_t)s_base + s_off[warp] + __popc(mask & ((1u << lane) - 1u)), s.P);
             for (int r = 0; r < 3; ++r) s.pos[dst][r * s.P + j] = x[r];
             s.pid[dst][j] = p;
             if (next) write_uniforms(s, ku, j, (uint64_t)p);
@@ -289,6 +289,7 @@ npm_status enqueue_frame(npm_wavefront* w, cudaStream_t st) {
 extern "C" {
 
 npm_status npm_wavefront_create(npm_handle* h, const npm_frame_config* cfg, npm_wavefront** out) {
+    npm::CallRange range("npm_wavefront_create");
     if (!h || !cfg || !out) return npm::set_error(NPM_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     if (h->cfg.mode != NPM_RADIANCE)
@@ -352,6 +353,7 @@ npm_status npm_wavefront_create(npm_handle* h, const npm_frame_config* cfg, npm_
 }
 
 npm_status npm_wavefront_run(npm_wavefront* w, int frames, void* stream, npm_frame_stats* out) {
+    npm::CallRange range("npm_wavefront_run");
     if (!w || frames < 0 || !out) return npm::set_error(NPM_ERR_INVALID_ARG, "bad argument");
     WfState& s = w->st;
     cudaStream_t st = (cudaStream_t)stream;

@@ -52,6 +52,23 @@ inline const float* inf_wfwd(const npm_handle* h) { return h->ema ? h->wfwd_inf 
 inline int* status_word(npm_handle* h) { return reinterpret_cast<int*>(h->scalars + 8); }
 
 namespace npm {
+// NVTX range named after an entry point for the lifetime of the object, so
+// that a profiler's timeline groups the kernels of each call (a few
+// nanoseconds when no tool is attached).
+struct CallRange {
+    explicit CallRange(const char* name);
+    ~CallRange();
+    CallRange(const CallRange&) = delete;
+    CallRange& operator=(const CallRange&) = delete;
+};
+
+// Test-only host-side fault injection, off unless the environment sets it:
+// NPM_TEST_FAIL_ALLOC=N makes the N-th device allocation of each npm_create
+// fail (NPM_ERR_OOM); NPM_TEST_FAIL_LAUNCH=N makes the N-th hot call of the
+// process report a failed launch (NPM_ERR_CUDA) without launching anything.
+cudaError_t device_alloc(void** p, size_t bytes);
+bool inject_launch_failure();
+
 // Validates cfg and derives the kernels' view of it; ng / nmlp receive the
 // grid and MLP parameter counts (npm_api.cu).
 npm_status make_devcfg(const npm_config* cfg, DevCfg* out, int64_t* ng, int64_t* nmlp);

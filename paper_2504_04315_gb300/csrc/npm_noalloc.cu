@@ -52,6 +52,7 @@ __global__ void k_noalloc_arrange(npm::DevCfg cfg, const float* __restrict__ mlp
 extern "C" npm_status npm_eval_pdf_noalloc(const npm_config* cfg, const float* params, int64_t n,
                                            const float* pos, const float* aux, const float* dir,
                                            int64_t ld, float* pdf_out, void* stream) {
+    npm::CallRange range("npm_eval_pdf_noalloc");
     npm::DevCfg dc;
     int64_t ng = 0, nmlp = 0;
     npm_status s = npm::make_devcfg(cfg, &dc, &ng, &nmlp);

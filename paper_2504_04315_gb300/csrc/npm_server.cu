@@ -317,6 +317,7 @@ npm_status submit(npm_server* s, Request* r, uint64_t* ticket) {
 extern "C" {
 
 npm_status npm_server_create(npm_handle* h, int64_t pool_queries, npm_server** out) {
+    npm::CallRange range("npm_server_create");
     if (!h || !out || pool_queries < 1) return npm::set_error(NPM_ERR_INVALID_ARG, "bad argument");
     *out = nullptr;
     npm_server* s = new npm_server();
@@ -348,6 +349,7 @@ npm_status npm_server_create(npm_handle* h, int64_t pool_queries, npm_server** o
 npm_status npm_server_submit_query(npm_server* s, int64_t n, const float* pos, const float* aux,
                                    const float* u, int64_t ld, float uniform_frac, float* dir_out,
                                    float* pdf_out, uint64_t* ticket) {
+    npm::CallRange range("npm_server_submit_query");
     if (!s || !ticket || n < 1 || ld < n || !pos || !u || !dir_out || !pdf_out ||
         (s->h->cfg.mode == NPM_PRODUCT && !aux) || !(uniform_frac >= 0.0f && uniform_frac <= 1.0f))
         return npm::set_error(NPM_ERR_INVALID_ARG, "bad query request");
@@ -368,6 +370,7 @@ npm_status npm_server_submit_query(npm_server* s, int64_t n, const float* pos, c
 npm_status npm_server_submit_train(npm_server* s, int64_t n, const float* pos, const float* aux,
                                    const float* dir, const float* radiance, const float* sample_pdf,
                                    int64_t ld, uint64_t* ticket) {
+    npm::CallRange range("npm_server_submit_train");
     if (!s || !ticket || n < 1 || ld < n || !pos || !dir || !radiance || !sample_pdf ||
         (s->h->cfg.mode == NPM_PRODUCT && !aux))
         return npm::set_error(NPM_ERR_INVALID_ARG, "bad training request");
@@ -387,6 +390,7 @@ npm_status npm_server_submit_train(npm_server* s, int64_t n, const float* pos, c
 }
 
 npm_status npm_server_wait(npm_server* s, uint64_t ticket, double* latency_ms) {
+    npm::CallRange range("npm_server_wait");
     if (!s) return npm::set_error(NPM_ERR_INVALID_ARG, "server is NULL");
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->all.find(ticket);
@@ -432,6 +436,7 @@ npm_status npm_server_get_stats(npm_server* s, npm_server_stats* out) {
 }
 
 npm_status npm_server_destroy(npm_server* s) {
+    npm::CallRange range("npm_server_destroy");
     if (!s) return NPM_OK;
     {
         std::lock_guard<std::mutex> lk(s->mu);

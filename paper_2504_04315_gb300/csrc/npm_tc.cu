@@ -71,7 +71,7 @@ __device__ __forceinline__ uint32_t corner_idx1(const DevCfg& cfg, int l, const 
     const uint32_t i = cl.c[0] + (c & 1), j = cl.c[1] + ((c >> 1) & 1), k = cl.c[2] + ((c >> 2) & 1);
     if ((cfg.dense_mask >> l) & 1u) {
         const uint32_t D = (uint32_t)cfg.level_res[l];
-        return i + D * (j + D * k);
+        return bounded_index(i + D * (j + D * k), D * D * D);
     }
     return (i ^ (j * 2654435761u) ^ (k * 805459861u)) & cfg.table_mask;
 }
@@ -1386,14 +1386,14 @@ npm_status tc_create(npm_handle* h) {
         tr.smem = tr.bar_off + 64;
         s->can_train = fits && pw <= 512 && tr.smem <= 220 * 1024;
     }
-    if (cudaMalloc(&s->wblob, nsplit * t.w_bytes) != cudaSuccess) {
+    if (device_alloc((void**)&s->wblob, nsplit * t.w_bytes) != cudaSuccess) {
         cudaGetLastError();
         delete s;
         return NPM_ERR_OOM;
     }
     cudaMemset(s->wblob, 0, nsplit * t.w_bytes);
     if (s->can_train && !t.split) {
-        if (cudaMalloc(&s->wblob_train, 2u * t.w_bytes) != cudaSuccess) {
+        if (device_alloc((void**)&s->wblob_train, 2u * t.w_bytes) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(s->wblob);
             delete s;
@@ -1403,7 +1403,7 @@ npm_status tc_create(npm_handle* h) {
     }
     if (s->can_train && c.feat_per_level == 2) {
         // Optional: without it the training kernel encodes in place.
-        if (cudaMalloc(&s->enc, sizeof(float) * (size_t)c.max_batch * h->dc.grid_feats) != cudaSuccess) {
+        if (device_alloc((void**)&s->enc, sizeof(float) * (size_t)c.max_batch * h->dc.grid_feats) != cudaSuccess) {
             cudaGetLastError();
             s->enc = nullptr;
         }

@@ -343,7 +343,8 @@ __global__ void __launch_bounds__(kThreads * kGroups, 1) k_forward_tiny(const __
             const Cell cl = make_cell(x, y, z, D);
             // Corners (x, x + 1) are adjacent entries: four row addresses,
             // the x-neighbour one entry on.
-            const uint2* r00 = sG + (cl.c[0] + uD * (cl.c[1] + uD * cl.c[2]));
+            // (the last corner, b + D^2 + D + 1, is below D^3 by the cell clamp)
+            const uint2* r00 = sG + bounded_index(cl.c[0] + uD * (cl.c[1] + uD * cl.c[2]), uD2 * uD - uD2 - uD - 1u);
             const uint2* rows[4] = {r00, r00 + uD, r00 + uD2, r00 + uD2 + uD};
             uint2 raw[8];
 #pragma unroll

@@ -47,6 +47,7 @@ __global__ void k_weighted_sum_f64(const float* __restrict__ pdf, const double* 
 npm_status npm_pdf_integral(npm_handle* h, int64_t n_pos, const float* pos, const float* aux, int64_t ld,
                             int64_t n_dir, const float* dirs, const double* weights, double* out,
                             void* stream) {
+    npm::CallRange range("npm_pdf_integral");
     if (!h) return npm::set_error(NPM_ERR_INVALID_ARG, "handle is NULL");
     if (n_pos < 0 || n_dir < 1 || ld < n_pos) return npm::set_error(NPM_ERR_INVALID_ARG, "bad sizes");
     if (n_pos > 0 && (!pos || !dirs || !weights || !out))

@@ -81,3 +81,9 @@ def test_null_handle_calls_are_errors(lib):
         == _lib.ERR_INVALID_ARG
     assert lib.npm_destroy(None) == _lib.OK
     assert lib.npm_num_params(None) == -1
+
+
+def test_normal_build_compiles_bounds_checks_out(lib):
+    # The bounds-checking kernels exist only in the debug build
+    # (_build.build_debug, NPM_DEBUG_BOUNDS); the normal build reports -1.
+    assert lib.npm_debug_bounds_violations() == -1
