@@ -17,7 +17,7 @@ from ._lib import NpmError  # noqa: F401
 
 RADIANCE, PRODUCT = 0, 1
 SOFTPLUS, EXP = 0, 1
-FP32, BF16, BF16X3 = 0, 1, 2
+FP32, BF16, BF16X3, FP16 = 0, 1, 2, 3
 
 
 def _torch():

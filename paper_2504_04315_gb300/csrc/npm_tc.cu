@@ -91,6 +91,7 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
                                           uint32_t lo, bool pad_all, int lbeg, int lend, bool tail) {
     const DevCfg& cfg = tc.base;
     const int kp = tc.layer[0].Kp;
+    const bool f16 = tc.f16 != 0;
     float x = 0.0f, y = 0.0f, z = 0.0f;
     if (valid) {
         x = pos[j];
@@ -133,10 +134,15 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
         uint32_t hw[4], lw[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            __nv_bfloat162 hb = __floats2bfloat162_rn(e[2 * i], e[2 * i + 1]);
-            hw[i] = *reinterpret_cast<uint32_t*>(&hb);
-            const float2 hf = __bfloat1622float2(hb);
-            lw[i] = pack_bf16(e[2 * i] - hf.x, e[2 * i + 1] - hf.y);
+            if (f16) {
+                hw[i] = pack_f16_sat(e[2 * i], e[2 * i + 1]);
+                lw[i] = 0u;
+            } else {
+                __nv_bfloat162 hb = __floats2bfloat162_rn(e[2 * i], e[2 * i + 1]);
+                hw[i] = *reinterpret_cast<uint32_t*>(&hb);
+                const float2 hf = __bfloat1622float2(hb);
+                lw[i] = pack_bf16(e[2 * i] - hf.x, e[2 * i + 1] - hf.y);
+            }
         }
         const uint32_t off = tile_off(row, 0, kp);
         *reinterpret_cast<uint4*>(sA + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -175,8 +181,8 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
                 b0 = fmaf(w1, v1[c].x, b0);
                 b1 = fmaf(w1, v1[c].y, b1);
             }
-            store_pair(sA, tile_off(row, 2 * l, kp), a0, a1, lo);
-            store_pair(sA, tile_off(row, 2 * l + 2, kp), b0, b1, lo);
+            store_pair(sA, tile_off(row, 2 * l, kp), a0, a1, lo, f16);
+            store_pair(sA, tile_off(row, 2 * l + 2, kp), b0, b1, lo, f16);
         }
     }
     for (; l < lend; ++l) {
@@ -197,7 +203,7 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
                 s0 = fmaf(w, v[c].x, s0);
                 s1 = fmaf(w, v[c].y, s1);
             }
-            store_pair(sA, tile_off(row, 2 * l, kp), s0, s1, lo);
+            store_pair(sA, tile_off(row, 2 * l, kp), s0, s1, lo, f16);
         } else if (F == 4 || F == 8) {
             // One vector load per corner and group of 4 features.
             uint32_t idx[8];
@@ -219,8 +225,8 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
                     acc.w = fmaf(w, v.w, acc.w);
                 }
                 const int k = l * F + 4 * h;
-                store_pair(sA, tile_off(row, k, kp), acc.x, acc.y, lo);
-                store_pair(sA, tile_off(row, k + 2, kp), acc.z, acc.w, lo);
+                store_pair(sA, tile_off(row, k, kp), acc.x, acc.y, lo, f16);
+                store_pair(sA, tile_off(row, k + 2, kp), acc.z, acc.w, lo, f16);
             }
         } else {
             // F = 1
@@ -230,7 +236,7 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
             corners8(cfg, l, cl, idx, ws);
 #pragma unroll
             for (int c = 0; c < 8; ++c) s = fmaf(ws[c], load_feat(gl + idx[c], 0), s);
-            store_one(sA, tile_off(row, l, kp), s, lo);
+            store_one(sA, tile_off(row, l, kp), s, lo, f16);
         }
     }
     if (!tail) return;
@@ -251,7 +257,7 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
         sh_band2(nn[0], nn[1], nn[2], e + 16);
         e[20] = r;
 #pragma unroll
-        for (int i = 0; i < 21; ++i) store_one(sA, tile_off(row, k + i, kp), e[i], lo);
+        for (int i = 0; i < 21; ++i) store_one(sA, tile_off(row, k + i, kp), e[i], lo, f16);
         k += 21;
     }
     const int kend = pad_all ? kp : min(kp, (k + 7) & ~7);
@@ -488,10 +494,11 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 
                                                          const __grid_constant__ QueryBatch qb,
                                                          int* __restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    const int nsplit = tc.split ? 2 : 1;
+    const int nsplit = tc.split ? 2 : 1;               // activation tiles (hi, residual)
+    const int nw = (tc.split || tc.f16) ? 2 : 1;       // weight blobs (hi, residual)
     uint8_t* sW = smem;
-    uint8_t* sA = smem + nsplit * (tc.w_bytes + tc.a0_bytes);  // inputs of layers >= 1
-    uint8_t* sA0 = tc.a0_bytes ? smem + nsplit * tc.w_bytes : sA;  // layer-0 input (encoding)
+    uint8_t* sA = smem + nw * tc.w_bytes + nsplit * tc.a0_bytes;  // inputs of layers >= 1
+    uint8_t* sA0 = tc.a0_bytes ? smem + nw * tc.w_bytes : sA;     // layer-0 input (encoding)
     const uint32_t a0_lo = tc.a0_bytes ? tc.a0_bytes : tc.a_bytes;  // its residual tile
     uint64_t* bars = reinterpret_cast<uint64_t*>(sA + nsplit * tc.a_bytes);  // [0] mma, [1] weights
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
@@ -520,7 +527,7 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 
 
     // Weights: one bulk asynchronous copy global -> shared.
     if (t == 0) {
-        const uint32_t wb = (uint32_t)nsplit * tc.w_bytes;
+        const uint32_t wb = (uint32_t)nw * tc.w_bytes;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_w), "r"(wb)
                      : "memory");
         asm volatile(
@@ -604,12 +611,15 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 
                     const uint64_t ad = umma_desc(a_addr + s * 256u, 128u, sbo);
                     const uint64_t bd = umma_desc(sW_addr + ly.w_off + s * 256u, 128u, sbo);
                     mma_bf16(tmem, ad, bd, ly.idesc, s > 0 ? 1u : 0u);
-                    if (tc.split) {
-                        // hi*lo and lo*hi residual products
+                    if (tc.split || tc.f16) {
+                        // hi*lo (the weights' residual) and, when split,
+                        // lo*hi (the activations' residual)
                         const uint64_t bdl = umma_desc(sW_addr + tc.w_bytes + ly.w_off + s * 256u, 128u, sbo);
-                        const uint64_t adl = umma_desc(a_addr + a_lo + s * 256u, 128u, sbo);
                         mma_bf16(tmem, ad, bdl, ly.idesc, 1u);
-                        mma_bf16(tmem, adl, bd, ly.idesc, 1u);
+                        if (tc.split) {
+                            const uint64_t adl = umma_desc(a_addr + a_lo + s * 256u, 128u, sbo);
+                            mma_bf16(tmem, adl, bd, ly.idesc, 1u);
+                        }
                     }
                 }
                 mma_commit(bar_mma);
@@ -633,7 +643,7 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] = fmaxf(__uint_as_float(r[i]), 0.0f);
                     store16_fwd(sA, tile_off(t, c0, kp_next), tile_off(t, c0 + 8, kp_next), v,
-                                tc.split ? tc.a_bytes : 0u);
+                                tc.split ? tc.a_bytes : 0u, tc.f16 != 0);
                 }
                 fence_async_smem();
                 tc_fence_before();
@@ -706,6 +716,14 @@ __global__ void k_tc_weights(TcCfg tc, const float* __restrict__ mlp, uint8_t* _
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
             const int nn = i / ly.Kp, k = i % ly.Kp;
             const float v = (nn < ly.N && k < ly.K) ? mlp[woff + (int64_t)nn * ly.K + k] : 0.0f;
+            if (tc.f16) {
+                // FP16 high part and FP16 residual (the weights to ~22 bits)
+                const __half hh = __float2half_rn(v);
+                *reinterpret_cast<__half*>(blob + ly.w_off + tile_off(nn, k, ly.Kp)) = hh;
+                *reinterpret_cast<__half*>(blob + tc.w_bytes + ly.w_off + tile_off(nn, k, ly.Kp)) =
+                    __float2half_rn(v - __half2float(hh));
+                continue;
+            }
             const __nv_bfloat16 hb = __float2bfloat16_rn(v);
             *reinterpret_cast<__nv_bfloat16*>(blob + ly.w_off + tile_off(nn, k, ly.Kp)) = hb;
             if (tc.split)
@@ -1304,10 +1322,11 @@ npm_status tc_create(npm_handle* h) {
         ly.Np = pad16(ly.N);
         ly.w_off = off;
         off += (uint32_t)(ly.Np * ly.Kp * 2);
-        // kind::f16 descriptor: D FP32 (bit 4), A and B BF16 (bits 7, 10),
-        // both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-        ly.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ly.Np >> 3) << 17) |
-                   ((uint32_t)(kTile >> 4) << 24);
+        // kind::f16 descriptor: D FP32 (bit 4), A and B BF16 (bits 7, 10;
+        // zero for FP16 operands), both K-major, N >> 3 at bit 17, M >> 4 at
+        // bit 24.
+        const uint32_t ab = c.precision == NPM_FP16 ? 0u : (1u << 7) | (1u << 10);
+        ly.idesc = (1u << 4) | ab | ((uint32_t)(ly.Np >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
         maxnp = ly.Np > maxnp ? ly.Np : maxnp;
     }
     t.w_bytes = (off + 127u) / 128u * 128u;
@@ -1325,12 +1344,14 @@ npm_status tc_create(npm_handle* h) {
     t.a_bytes = (uint32_t)(kTile * maxkp1 * 2);
     t.a0_bytes = sep0 ? (uint32_t)(kTile * t.layer[0].Kp * 2) : 0u;
     t.split = c.precision == NPM_BF16X3 ? 1 : 0;
+    t.f16 = c.precision == NPM_FP16 ? 1 : 0;
     const uint32_t nsplit = t.split ? 2u : 1u;
+    const uint32_t nw = (t.split || t.f16) ? 2u : 1u;
     uint32_t cols = 32;
     while ((int)cols < maxnp) cols <<= 1;
     t.tmem_cols = cols;
     t.enc_width = enc_width;
-    s->smem = nsplit * (t.w_bytes + t.a0_bytes + t.a_bytes) + 64;
+    s->smem = nw * t.w_bytes + nsplit * (t.a0_bytes + t.a_bytes) + 64;
     if (s->smem > 200 * 1024 || c.K > 16) {
         delete s;
         return NPM_ERR_UNSUPPORTED;
@@ -1343,6 +1364,9 @@ npm_status tc_create(npm_handle* h) {
         TcTrain& tr = s->train;
         memset(&tr, 0, sizeof(tr));
         s->train_cfg = t;
+        // Training multiplies BF16 operands whatever the inference format.
+        s->train_cfg.f16 = 0;
+        for (int l = 0; l < c.n_layers; ++l) s->train_cfg.layer[l].idesc |= (1u << 7) | (1u << 10);
         uint32_t off = 2u * t.w_bytes, col0 = 0, cols = 0;
         int64_t wo = 0;
         bool fits = c.K * 4 <= 64 && c.n_levels * c.feat_per_level <= 32;
@@ -1386,12 +1410,12 @@ npm_status tc_create(npm_handle* h) {
         tr.smem = tr.bar_off + 64;
         s->can_train = fits && pw <= 512 && tr.smem <= 220 * 1024;
     }
-    if (device_alloc((void**)&s->wblob, nsplit * t.w_bytes) != cudaSuccess) {
+    if (device_alloc((void**)&s->wblob, nw * t.w_bytes) != cudaSuccess) {
         cudaGetLastError();
         delete s;
         return NPM_ERR_OOM;
     }
-    cudaMemset(s->wblob, 0, nsplit * t.w_bytes);
+    cudaMemset(s->wblob, 0, nw * t.w_bytes);
     if (s->can_train && !t.split) {
         if (device_alloc((void**)&s->wblob_train, 2u * t.w_bytes) != cudaSuccess) {
             cudaGetLastError();
@@ -1428,7 +1452,7 @@ cudaError_t tc_refresh_weights(npm_handle* h, cudaStream_t st) {
     if (s->wblob_train) k_tc_weights<<<16, 256, 0, st>>>(s->train_cfg, h->params + h->mlp_off, s->wblob_train);
     if (h->ema) {
         if (!s->wblob_inf) {
-            const size_t bytes = (s->cfg.split ? 2u : 1u) * (size_t)s->cfg.w_bytes;
+            const size_t bytes = ((s->cfg.split || s->cfg.f16) ? 2u : 1u) * (size_t)s->cfg.w_bytes;
             cudaError_t e = cudaMalloc(&s->wblob_inf, bytes);
             if (e != cudaSuccess) return e;
             cudaMemsetAsync(s->wblob_inf, 0, bytes, st);

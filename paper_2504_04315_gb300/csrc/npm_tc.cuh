@@ -33,6 +33,8 @@ struct TcCfg {
                        // buffer (the encoding leaves all-zero 8-column chunks);
                        // 0 when layer 0 shares the buffer of layers >= 1
     int split;         // 1: BF16 residual operands (three MMAs per K step)
+    int f16;           // 1: FP16 operands: activations rounded to FP16, weights
+                       // FP16 plus an FP16 residual (two MMAs per K step)
     uint32_t tmem_cols;
     int enc_width;     // meaningful network inputs
 };
@@ -135,6 +137,19 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// (a, b) rounded to nearest FP16 and packed (a in the low half); values
+// beyond the FP16 range saturate to +-65504 rather than becoming infinite.
+__device__ __forceinline__ uint32_t pack_f16_sat(float a, float b) {
+    uint32_t d;
+    asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+    return d;
+}
+
+// A pair of MMA operands in the model's operand format.
+__device__ __forceinline__ uint32_t pack_op(float a, float b, bool f16) {
+    return f16 ? pack_f16_sat(a, b) : pack_bf16(a, b);
+}
+
 // Byte offset of element (row, k) in a K-major no-swizzle tile whose rows
 // hold kp elements: 8x8 core matrices (128 bytes), K-adjacent core matrices
 // 128 bytes apart, 8-row groups kp/8 * 128 bytes apart.
@@ -167,11 +182,14 @@ __device__ __forceinline__ void store16(uint8_t* sA, uint32_t off0, uint32_t off
 // v - hi, exact in FP32 and of the same sign as v, is rounded to BF16 (one
 // packed subtraction and one conversion per pair); the product error that
 // split BF16 drops stays below 2^-15 relative. Without a residual tile, v is
-// rounded to nearest.
+// rounded to nearest (to FP16 with saturation when f16).
 __device__ __forceinline__ void store16_fwd(uint8_t* sA, uint32_t off0, uint32_t off1, const float (&v)[16],
-                                            uint32_t lo_off) {
+                                            uint32_t lo_off, bool f16 = false) {
     uint32_t h[8];
-    if (lo_off) {
+    if (f16) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) h[i] = pack_f16_sat(v[2 * i], v[2 * i + 1]);
+    } else if (lo_off) {
         uint32_t l[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -192,8 +210,14 @@ __device__ __forceinline__ void store16_fwd(uint8_t* sA, uint32_t off0, uint32_t
     *reinterpret_cast<uint4*>(sA + off1) = make_uint4(h[4], h[5], h[6], h[7]);
 }
 
-// One or two BF16 values (and their residuals when lo_off != 0).
-__device__ __forceinline__ void store_pair(uint8_t* sA, uint32_t off, float a, float b, uint32_t lo_off) {
+// One or two BF16 values (and their residuals when lo_off != 0), or FP16
+// values when f16.
+__device__ __forceinline__ void store_pair(uint8_t* sA, uint32_t off, float a, float b, uint32_t lo_off,
+                                           bool f16 = false) {
+    if (f16) {
+        *reinterpret_cast<uint32_t*>(sA + off) = pack_f16_sat(a, b);
+        return;
+    }
     __nv_bfloat162 hb = __floats2bfloat162_rn(a, b);
     *reinterpret_cast<__nv_bfloat162*>(sA + off) = hb;
     if (lo_off) {
@@ -202,7 +226,11 @@ __device__ __forceinline__ void store_pair(uint8_t* sA, uint32_t off, float a, f
     }
 }
 
-__device__ __forceinline__ void store_one(uint8_t* sA, uint32_t off, float a, uint32_t lo_off) {
+__device__ __forceinline__ void store_one(uint8_t* sA, uint32_t off, float a, uint32_t lo_off, bool f16 = false) {
+    if (f16) {
+        *reinterpret_cast<uint16_t*>(sA + off) = (uint16_t)(pack_f16_sat(a, 0.0f) & 0xffffu);
+        return;
+    }
     const __nv_bfloat16 hb = __float2bfloat16_rn(a);
     *reinterpret_cast<__nv_bfloat16*>(sA + off) = hb;
     if (lo_off)

@@ -1,7 +1,8 @@
 // npm_tc_tiny.cu -- fused tensor-core forward for the small serving networks:
 // one dense grid level of 4 FP16 features, three bias-free layers of at most
-// 32 outputs (tcgen05.mma, BF16 operands, FP32 accumulation in tensor memory)
-// and K = 4 vMF lobes (the reduced-precision serving workload).
+// 32 outputs (tcgen05.mma on BF16, split BF16 or FP16 operands, FP32
+// accumulation in tensor memory) and K = 4 vMF lobes (the reduced-precision
+// serving workload).
 //
 // The general kernel (npm_tc.cu) serves every shape; this one trims the
 // per-query instruction count of the shape the serving loop runs, where the
@@ -84,9 +85,21 @@ __device__ __forceinline__ float2 bf16x2_to_f2(uint32_t h) {
     return make_float2(__uint_as_float(h << 16), __uint_as_float(h & 0xffff0000u));
 }
 
-template <bool SPLIT>
+// Operand formats of the tiny kernel: BF16, BF16 split into high part and
+// residual, FP16 (weights FP16 plus an FP16 residual).
+enum : int { kOpsBf16 = 0, kOpsBf16x3 = 1, kOpsFp16 = 2 };
+
+__device__ __forceinline__ uint32_t cvt_f16_relu(float v0, float v1) {
+    uint32_t d;
+    asm("cvt.rn.satfinite.relu.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(v1), "f"(v0));
+    return d;
+}
+
+template <int OPS>
 __device__ __forceinline__ void relu_pair(float v0, float v1, uint32_t& hi, uint32_t& lo) {
-    if (SPLIT) {
+    if (OPS == kOpsFp16) {
+        hi = cvt_f16_relu(v0, v1);
+    } else if (OPS == kOpsBf16x3) {
         hi = cvt_rz_relu(v0, v1);
         const float2 r = fma2(bf16x2_to_f2(hi), f2(-1.0f), make_float2(v0, v1));
         lo = cvt_rn_relu(r.x, r.y);
@@ -97,10 +110,14 @@ __device__ __forceinline__ void relu_pair(float v0, float v1, uint32_t& hi, uint
 
 // Encoding features (any sign): high parts rounded to nearest, residuals
 // v - hi rounded to nearest.
-template <bool SPLIT>
+template <int OPS>
 __device__ __forceinline__ void feat_pair(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+    if (OPS == kOpsFp16) {
+        hi = pack_f16_sat(v0, v1);
+        return;
+    }
     hi = cvt_rn(v0, v1);
-    if (SPLIT) {
+    if (OPS == kOpsBf16x3) {
         const float2 r = fma2(bf16x2_to_f2(hi), f2(-1.0f), make_float2(v0, v1));
         lo = cvt_rn(r.x, r.y);
     }
@@ -221,16 +238,17 @@ struct TinyLayout {
 
 __host__ __device__ inline TinyLayout tiny_layout(const TcCfg& c, uint32_t grid_bytes) {
     TinyLayout L;
-    const uint32_t nsplit = c.split ? 2u : 1u;
-    L.grid = nsplit * c.w_bytes;                            // weights first (hi, then lo)
+    const uint32_t nw = (c.split || c.f16) ? 2u : 1u;       // weight blobs
+    const uint32_t na = c.split ? 2u : 1u;                  // activation tiles
+    L.grid = nw * c.w_bytes;                                // weights first (hi, then lo)
     L.a = (L.grid + grid_bytes + 1023u) & ~1023u;           // per-group activation tiles
-    L.a_stride = nsplit * c.a_bytes;                        // hi tile, then its residual
+    L.a_stride = na * c.a_bytes;                            // hi tile, then its residual
     L.bars = L.a + (uint32_t)kGroups * L.a_stride;          // [0] weights + grid, [1 + g] MMA
     L.bytes = L.bars + 8u * (1u + kGroups) + 16u;           // + tensor-memory slot
     return L;
 }
 
-template <bool SPLIT>
+template <int OPS>
 __global__ void __launch_bounds__(kThreads * kGroups, 1) k_forward_tiny(const __grid_constant__ TcCfg tc,
                                                                         const uint2* __restrict__ grid4,
                                                                         uint32_t grid_bytes,
@@ -238,7 +256,8 @@ __global__ void __launch_bounds__(kThreads * kGroups, 1) k_forward_tiny(const __
                                                                         const __grid_constant__ QueryBatch qb,
                                                                         int* __restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    constexpr int nsplit = SPLIT ? 2 : 1;
+    constexpr bool SPLIT = OPS == kOpsBf16x3;
+    constexpr int nw = OPS == kOpsBf16 ? 1 : 2;  // weight blobs (hi, residual)
     const TinyLayout lay = tiny_layout(tc, grid_bytes);
     const int g = threadIdx.x >> 7;      // tile group
     const int t = threadIdx.x & 127;     // row of the group's tile
@@ -269,7 +288,7 @@ __global__ void __launch_bounds__(kThreads * kGroups, 1) k_forward_tiny(const __
     const uint32_t tmem = *tslot + 32u * (uint32_t)g;
     if (threadIdx.x == 0) {
         // Weights and grid table: two bulk copies on one barrier.
-        const uint32_t wb = (uint32_t)nsplit * tc.w_bytes;
+        const uint32_t wb = (uint32_t)nw * tc.w_bytes;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_w), "r"(wb + grid_bytes)
                      : "memory");
         asm volatile(
@@ -360,8 +379,8 @@ __global__ void __launch_bounds__(kThreads * kGroups, 1) k_forward_tiny(const __
                 a23 = fma2(f2(w8[c]), v23, a23);
             }
             uint32_t h01, h23, l01 = 0u, l23 = 0u;
-            feat_pair<SPLIT>(a01.x, a01.y, h01, l01);
-            feat_pair<SPLIT>(a23.x, a23.y, h23, l23);
+            feat_pair<OPS>(a01.x, a01.y, h01, l01);
+            feat_pair<OPS>(a23.x, a23.y, h23, l23);
             *reinterpret_cast<uint4*>(sA + row16) = make_uint4(h01, h23, 0u, 0u);
             *reinterpret_cast<uint4*>(sA + row16 + 128) = make_uint4(0u, 0u, 0u, 0u);
             if (SPLIT) {
@@ -388,10 +407,8 @@ __global__ void __launch_bounds__(kThreads * kGroups, 1) k_forward_tiny(const __
                     if (s < (ly.Kp >> 4)) {
                         const uint64_t o = (uint64_t)(16 * s);
                         mma_bf16(tmem, ad + o, bd + o, ly.idesc, s > 0 ? 1u : 0u);
-                        if (SPLIT) {
-                            mma_bf16(tmem, ad + o, bl + o, ly.idesc, 1u);
-                            mma_bf16(tmem, al + o, bd + o, ly.idesc, 1u);
-                        }
+                        if (OPS != kOpsBf16) mma_bf16(tmem, ad + o, bl + o, ly.idesc, 1u);
+                        if (SPLIT) mma_bf16(tmem, al + o, bd + o, ly.idesc, 1u);
                     }
                 }
                 mma_commit(bar_mma);
@@ -416,7 +433,7 @@ __global__ void __launch_bounds__(kThreads * kGroups, 1) k_forward_tiny(const __
                         uint32_t hi[8], lo[8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i)
-                            relu_pair<SPLIT>(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]), hi[i], lo[i]);
+                            relu_pair<OPS>(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]), hi[i], lo[i]);
                         const uint32_t o = row32 + (uint32_t)(c0 >> 3) * 128u;
                         *reinterpret_cast<uint4*>(sA + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
                         *reinterpret_cast<uint4*>(sA + o + 128) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
@@ -545,13 +562,14 @@ bool tiny_qualifies(const TcCfg& c) {
 
 cudaError_t launch_tiny(const TcCfg& c, size_t, const __half* grid_h, const uint8_t* wblob, QueryBatch& qb,
                         int64_t max_n, int* status, cudaStream_t st) {
-    auto kern = c.split ? k_forward_tiny<true> : k_forward_tiny<false>;
+    auto kern = c.split ? k_forward_tiny<kOpsBf16x3> : c.f16 ? k_forward_tiny<kOpsFp16> : k_forward_tiny<kOpsBf16>;
     const uint32_t grid_bytes = (uint32_t)c.base.level_res[0] * c.base.level_res[0] * c.base.level_res[0] * 8u;
     const size_t smem = tiny_layout(c, grid_bytes).bytes;
     // One CTA per SM (kGroups x 128 threads at 64 registers); carve out just
     // its shared memory so the rest stays L1.
-    static std::atomic<uint64_t> attrs_s{~0ull}, attrs_p{~0ull};
-    cudaError_t e = set_smem_attrs(kern, smem, carveout_percent(smem + 1024), c.split ? attrs_s : attrs_p);
+    static std::atomic<uint64_t> attrs_s{~0ull}, attrs_h{~0ull}, attrs_p{~0ull};
+    cudaError_t e = set_smem_attrs(kern, smem, carveout_percent(smem + 1024),
+                                   c.split ? attrs_s : c.f16 ? attrs_h : attrs_p);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);

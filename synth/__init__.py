@@ -83,7 +83,7 @@ RES16 = [16, 20, 25, 32, 40, 50, 64, 80, 101, 128, 161, 203, 256, 322, 406, 512]
 
 RADIANCE, PRODUCT = 0, 1
 SOFTPLUS, EXP = 0, 1
-FP32, BF16, BF16X3 = 0, 1, 2
+FP32, BF16, BF16X3, FP16 = 0, 1, 2, 3
 
 
 @dataclass

@@ -32,6 +32,7 @@ def _need_cuda():
                                              (synth.PAPER_HASH, synth.FP32, 1e-4),
                                              (PRODUCT_SMALL, synth.FP32, 1e-4),
                                              (synth.TINY_BF16, synth.BF16X3, 2e-2),
+                                             (synth.TINY_BF16, synth.FP16, 2e-2),
                                              (synth.PAPER_HASH, synth.BF16X3, 2e-2)])
 def test_log_pdf_matches_oracle(w, precision, tol):
     n = 4096

@@ -129,7 +129,7 @@ def _designed(w, n, seed):
     return params, pos, synth.sample_uniforms(seed, n, rows=4)
 
 
-@pytest.mark.parametrize("precision", [synth.BF16X3, synth.BF16], ids=["split-bf16", "bf16"])
+@pytest.mark.parametrize("precision", [synth.BF16X3, synth.BF16, synth.FP16], ids=["split-bf16", "bf16", "fp16"])
 @pytest.mark.parametrize("ufrac", [0.0, 0.3])
 def test_rp_sampler_stage_designed_mixture(precision, ufrac):
     w = synth.TINY_BF16.with_(precision=precision)
@@ -145,7 +145,9 @@ def test_rp_sampler_stage_designed_mixture(precision, ufrac):
 
 @pytest.mark.parametrize("w,n", [(synth.TINY_BF16, 1 << 16),
                                  (synth.TINY_BF16.with_(precision=synth.BF16), 1 << 16),
+                                 (synth.TINY_BF16.with_(precision=synth.FP16), 1 << 16),
                                  (synth.PAPER_HASH.with_(precision=synth.BF16X3), 1 << 14),
+                                 (synth.PAPER_HASH.with_(precision=synth.FP16), 1 << 14),
                                  (synth.PAPER_OWN.with_(precision=synth.BF16X3), 1 << 14),
                                  (PRODUCT_SMALL.with_(precision=synth.BF16X3), 4096),
                                  (synth.PRODUCT_BF16, 1 << 14)])
@@ -160,20 +162,22 @@ def test_rp_sampler_stage_random_models(w, n):
     _stage_check(host(mix), u, host(d).astype(np.float64), w.K)
 
 
+@pytest.mark.parametrize("precision", [synth.BF16X3, synth.FP16], ids=["split-bf16", "fp16"])
 @pytest.mark.parametrize("w,n", [(synth.TINY_BF16, 1 << 16),
-                                 (synth.PAPER_HASH.with_(precision=synth.BF16X3), 1 << 14),
-                                 (synth.PAPER_OWN.with_(precision=synth.BF16X3), 1 << 14),
-                                 (PRODUCT_SMALL.with_(precision=synth.BF16X3), 4096),
+                                 (synth.PAPER_HASH, 1 << 14),
+                                 (synth.PAPER_OWN, 1 << 14),
+                                 (PRODUCT_SMALL, 4096),
                                  (synth.PRODUCT_BF16, 1 << 14)])
-def test_rp_directions_match_oracle(w, n):
+def test_rp_directions_match_oracle(w, n, precision):
     params = synth.random_params(w, 43)
     pos = synth.positions(43, n)
     u = synth.sample_uniforms(43, n)
     aux = synth.aux_inputs(43, n) if w.mode == synth.PRODUCT else None
-    m = make_model(w, params, n, precision=synth.BF16X3)
+    m = make_model(w, params, n, precision=precision)
     d, _, _ = m.query_sample(cuda(pos), cuda(u), None if aux is None else cuda(aux))
     m.check_device_status()
-    compare_rp_directions(w, params, pos, u, aux, host(d).astype(np.float64))
+    compare_rp_directions(w, params, pos, u, aux, host(d).astype(np.float64),
+                          median_bar=3e-4 if precision == synth.BF16X3 else 1e-3)
 
 
 def test_rp_directions_designed_mixture_match_oracle():
@@ -186,13 +190,14 @@ def test_rp_directions_designed_mixture_match_oracle():
     compare_rp_directions(w, params, pos, u[:3], None, host(d).astype(np.float64))
 
 
-def test_rp_chi_square_against_oracle_density():
-    # 10^6 split-BF16 samples at X0 against the oracle's V integrated over
+@pytest.mark.parametrize("precision", [synth.BF16X3, synth.FP16], ids=["split-bf16", "fp16"])
+def test_rp_chi_square_against_oracle_density(precision):
+    # 10^6 tensor-core samples at X0 against the oracle's V integrated over
     # 64 x 128 equal-area bins.
     w = synth.TINY_BF16
     n = 1_000_000
     params, pos, u = _designed(w, n, 45)
-    m = make_model(w, params, n, precision=synth.BF16X3)
+    m = make_model(w, params, n, precision=precision)
     d, _, _ = m.query_sample(cuda(pos), cuda(u[:3].copy()))
     m.check_device_status()
     gd = host(d).astype(np.float64)

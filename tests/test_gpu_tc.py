@@ -89,18 +89,22 @@ def test_tc_bf16_single_matches_quantisation_model(n):
     assert np.quantile(e_model, 0.999) <= PDF_P999_BF16_MODEL
 
 
+@pytest.mark.parametrize("precision", [synth.BF16X3, synth.FP16], ids=["split-bf16", "fp16"])
 @pytest.mark.parametrize("w,n", [(synth.TINY_BF16, 1 << 16),
-                                 (synth.PAPER_HASH.with_(precision=synth.BF16X3), 1 << 14),
-                                 (synth.PAPER_OWN.with_(precision=synth.BF16X3), 1 << 14),
-                                 (PRODUCT_SMALL.with_(precision=synth.BF16X3), 4096),
-                                 (synth.PRODUCT_BF16.with_(precision=synth.BF16X3), 1 << 14)])
-def test_tc_split_bf16_parity(w, n):
+                                 (synth.PAPER_HASH, 1 << 14),
+                                 (synth.PAPER_OWN, 1 << 14),
+                                 (PRODUCT_SMALL, 4096),
+                                 (synth.PRODUCT_BF16, 1 << 14)])
+def test_tc_reduced_precision_parity(w, n, precision):
     # Split BF16 (hi + residual operands, three MMAs per K step): the error
-    # left is the FP16 rounding of the grid features.
-    err, gm, om, _, _, _, _ = _bf16_stats(w, n, 22, precision=synth.BF16X3)
-    print(f"bf16x3 {w.name[:30]} n={n} pdf err p50 {np.median(err):.2e} p99.9 "
+    # left is the FP16 rounding of the grid features. FP16 operands (weights
+    # with an FP16 residual, two MMAs per K step): the FP16 rounding of the
+    # activations as well.
+    w = w.with_(precision=precision)
+    err, gm, om, _, _, _, _ = _bf16_stats(w, n, 22, precision=precision)
+    print(f"precision {precision} {w.name[:30]} n={n} pdf err p50 {np.median(err):.2e} p99.9 "
           f"{np.quantile(err, 0.999):.2e} max {err.max():.2e}")
-    assert np.quantile(err, 0.999) <= 1e-2
+    assert np.quantile(err, 0.999) <= (1e-2 if precision == synth.BF16X3 else PDF_P999_BF16)
     assert np.median(err) <= 1e-3
 
 
@@ -118,11 +122,11 @@ def test_tc_bf16_single_eval_pdf_matches_quantisation_model(dirs_from):
     assert np.quantile(e_model, 0.999) <= PDF_P999_BF16_MODEL
 
 
+@pytest.mark.parametrize("precision", [synth.BF16X3, synth.FP16], ids=["split-bf16", "fp16"])
 @pytest.mark.parametrize("dirs_from", ["mixture", "uniform"])
-def test_tc_eval_pdf_matches_oracle(dirs_from):
-    # Split BF16 density at directions drawn from the mixture (where the
-    # guide is used) and uniformly.
-    precision = synth.BF16X3
+def test_tc_eval_pdf_matches_oracle(dirs_from, precision):
+    # Split BF16 and FP16 densities at directions drawn from the mixture
+    # (where the guide is used) and uniformly.
     w = synth.TINY_BF16
     n = 4096
     params = synth.random_params(w, 23)
@@ -136,7 +140,7 @@ def test_tc_eval_pdf_matches_oracle(dirs_from):
     got = host(m.eval_pdf(cuda(pos), cuda(dirs)))
     ref = oracle.eval_pdf(w, params, pos, dirs)
     err = np.abs(got - ref) / np.maximum(ref, FLOOR)
-    print(f"eval split bf16 dirs={dirs_from}: p99.9 {np.quantile(err, 0.999):.2e}")
+    print(f"eval precision {precision} dirs={dirs_from}: p99.9 {np.quantile(err, 0.999):.2e}")
     assert np.quantile(err, 0.999) <= PDF_P999_BF16
 
 
@@ -144,7 +148,9 @@ def test_tc_eval_pdf_matches_oracle(dirs_from):
                                  (synth.PAPER_HASH.with_(precision=synth.BF16X3), 4096),
                                  (synth.PAPER_OWN.with_(precision=synth.BF16X3), 4096),
                                  (synth.PRODUCT_BF16, 3000),
-                                 (synth.TINY_BF16.with_(precision=synth.BF16), 4096)])
+                                 (synth.TINY_BF16.with_(precision=synth.BF16), 4096),
+                                 (synth.TINY_BF16.with_(precision=synth.FP16), 4096),
+                                 (synth.PAPER_HASH.with_(precision=synth.FP16), 4096)])
 def test_tc_gradient_parity(w, n):
     # Training on tensor cores (FP32 TMEM accumulation, split BF16
     # operands in both reduced-precision modes) against the FP64 oracle
@@ -178,8 +184,9 @@ def test_tc_gradient_parity(w, n):
     assert abs(float(host(l2)[0]) - loss) <= bar * abs(loss)
 
 
-@pytest.mark.parametrize("w", [synth.TINY_BF16, synth.PAPER_HASH.with_(precision=synth.BF16X3)],
-                         ids=["tiny-split-bf16", "paper-hash-split-bf16"])
+@pytest.mark.parametrize("w", [synth.TINY_BF16, synth.PAPER_HASH.with_(precision=synth.BF16X3),
+                               synth.TINY_BF16.with_(precision=synth.FP16)],
+                         ids=["tiny-split-bf16", "paper-hash-split-bf16", "tiny-fp16"])
 def test_tc_kl_estimate_matches_oracle(w):
     # KL estimate of the guide against the noise-free target on a seeded
     # 2^16 subset: (1/N) sum_j (D_j / p_j) (log D_j - log V_j), directions
@@ -206,12 +213,13 @@ def test_tc_kl_estimate_matches_oracle(w):
     assert abs(kl_g - kl_o) <= 1e-3
 
 
-def test_tc_tiny_full_size_launch_sampled():
+@pytest.mark.parametrize("precision", [synth.BF16X3, synth.FP16], ids=["split-bf16", "fp16"])
+def test_tc_tiny_full_size_launch_sampled(precision):
     # The reduced-precision workload as the benchmark launches it: 2^22
-    # queries in one call, split BF16; the oracle checks a seeded 2^16 subset:
-    # the density at the GPU-sampled directions and the directions
-    # themselves (oracle.query_sample on the same uniforms).
-    w = synth.TINY_BF16
+    # queries in one call; the oracle checks a seeded 2^16 subset: the
+    # density at the GPU-sampled directions and the directions themselves
+    # (oracle.query_sample on the same uniforms).
+    w = synth.TINY_BF16.with_(precision=precision)
     n = w.n_query
     params = synth.random_params(w, 3)
     pos = synth.positions(0, n)
@@ -227,4 +235,5 @@ def test_tc_tiny_full_size_launch_sampled():
     err = np.abs(gp[pick] - ref) / np.maximum(ref, FLOOR)
     print(f"tiny 2^22 launch, 2^16 subset: p99.9 {np.quantile(err, 0.999):.2e} max {err.max():.2e}")
     assert np.quantile(err, 0.999) <= PDF_P999_BF16
-    compare_rp_directions(w, params, pos[:, pick], u[:, pick], None, gd[:, pick].astype(np.float64))
+    compare_rp_directions(w, params, pos[:, pick], u[:, pick], None, gd[:, pick].astype(np.float64),
+                          median_bar=3e-4 if precision == synth.BF16X3 else 1e-3)
