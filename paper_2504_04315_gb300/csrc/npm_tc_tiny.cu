@@ -208,11 +208,10 @@ __device__ __forceinline__ float2 pair_log_terms(const LobePair& L, float2 logit
 }
 
 // Tile groups per CTA: one CTA per SM, each group of 128 threads walks its
-// own tiles with its own activation tiles, tensor-memory columns, MMA
-// barriers and named CTA barrier, sharing one copy of the weights and of
-// the grid table in shared memory. A group keeps P tiles in flight: while
-// one tile's layer runs on the tensor cores, the group converts, encodes or
-// decodes another, so the MMA round trips overlap its own work.
+// own tiles with its own activation tile, tensor-memory columns, MMA
+// barrier and named CTA barrier, sharing one copy of the weights and of the
+// grid table in shared memory.
+constexpr int kGroups = 8;
 
 // Named barrier of group g (id 0 is the CTA-wide __syncthreads).
 __device__ __forceinline__ void group_sync(int g) {
@@ -232,251 +231,61 @@ __device__ __forceinline__ bool group_sync_or(int g, bool p) {
     return r != 0;
 }
 
-// Shared-memory layout of the CTA (byte offsets) for G groups of P tiles.
+// Shared-memory layout of the CTA (byte offsets).
 struct TinyLayout {
     uint32_t grid, a, a_stride, bars, bytes;
 };
 
-__host__ __device__ inline TinyLayout tiny_layout(const TcCfg& c, uint32_t grid_bytes, int G, int P) {
+__host__ __device__ inline TinyLayout tiny_layout(const TcCfg& c, uint32_t grid_bytes) {
     TinyLayout L;
     const uint32_t nw = (c.split || c.f16) ? 2u : 1u;       // weight blobs
     const uint32_t na = c.split ? 2u : 1u;                  // activation tiles
     L.grid = nw * c.w_bytes;                                // weights first (hi, then lo)
-    L.a = (L.grid + grid_bytes + 1023u) & ~1023u;           // activation tiles, slot-major
+    L.a = (L.grid + grid_bytes + 1023u) & ~1023u;           // per-group activation tiles
     L.a_stride = na * c.a_bytes;                            // hi tile, then its residual
-    L.bars = L.a + (uint32_t)(G * P) * L.a_stride;          // [0] weights + grid, [1 + slot] MMA
-    L.bytes = L.bars + 8u * (1u + (uint32_t)(G * P)) + 16u; // + tensor-memory slot
+    L.bars = L.a + (uint32_t)kGroups * L.a_stride;          // [0] weights + grid, [1 + g] MMA
+    L.bytes = L.bars + 8u * (1u + kGroups) + 16u;           // + tensor-memory slot
     return L;
 }
 
-// The segment of a tile of a query batch: its request, valid rows and the
-// batch row of the tile's first query.
-struct TileSeg {
-    const QuerySeg* S;
-    int64_t n, row0;
-};
-
-__device__ __forceinline__ TileSeg tile_seg(const QueryBatch& qb, int64_t tile, int64_t n0) {
-    int sg = 0;
-    while (sg + 1 < qb.nseg && tile >= qb.seg[sg + 1].tile0) ++sg;
-    TileSeg ts;
-    ts.S = &qb.seg[sg];
-    ts.n = (sg == 0 && qb.n_dev) ? n0 : ts.S->n;
-    ts.row0 = (tile - ts.S->tile0) * kTile;
-    return ts;
-}
-
-// Encode (Sec. 5.1, Eq. 11): the 8 corners of row t's cell from the
-// shared-memory table, blended in FP32, written as the row's first 8-column
-// chunk (4 features, 4 zeros); the second chunk of the 16-column input is
-// zero.
 template <int OPS>
-__device__ __forceinline__ void tiny_encode(const TileSeg& ts, int t, const uint2* sG, uint32_t D, uint8_t* sA,
-                                            uint32_t row16, uint32_t lo_off) {
-    const QuerySeg& S = *ts.S;
-    const int64_t j = ts.row0 + t, ld = S.ld;
-    float x = 0.0f, y = 0.0f, z = 0.0f;
-    if (j < ts.n) {
-        x = S.pos[j];
-        y = S.pos[ld + j];
-        z = S.pos[2 * ld + j];
-    }
-    const Cell cl = make_cell(x, y, z, (int)D);
-    const uint32_t D2 = D * D;
-    // Corners (x, x + 1) are adjacent entries: four row addresses, the
-    // x-neighbour one entry on (the last corner, b + D^2 + D + 1, is below
-    // D^3 by the cell clamp).
-    const uint2* r00 = sG + bounded_index(cl.c[0] + D * (cl.c[1] + D * cl.c[2]), D2 * D - D2 - D - 1u);
-    const uint2* rows[4] = {r00, r00 + D, r00 + D2, r00 + D2 + D};
-    uint2 raw[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) raw[c] = rows[c >> 1][c & 1];
-    float w8[8];
-    corner_w8(cl, w8);
-    float2 a01 = make_float2(0.0f, 0.0f), a23 = make_float2(0.0f, 0.0f);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const float2 v01 = __half22float2(*reinterpret_cast<const __half2*>(&raw[c].x));
-        const float2 v23 = __half22float2(*reinterpret_cast<const __half2*>(&raw[c].y));
-        a01 = fma2(f2(w8[c]), v01, a01);
-        a23 = fma2(f2(w8[c]), v23, a23);
-    }
-    uint32_t h01, h23, l01 = 0u, l23 = 0u;
-    feat_pair<OPS>(a01.x, a01.y, h01, l01);
-    feat_pair<OPS>(a23.x, a23.y, h23, l23);
-    *reinterpret_cast<uint4*>(sA + row16) = make_uint4(h01, h23, 0u, 0u);
-    *reinterpret_cast<uint4*>(sA + row16 + 128) = make_uint4(0u, 0u, 0u, 0u);
-    if (OPS == kOpsBf16x3) {
-        *reinterpret_cast<uint4*>(sA + lo_off + row16) = make_uint4(l01, l23, 0u, 0u);
-        *reinterpret_cast<uint4*>(sA + lo_off + row16 + 128) = make_uint4(0u, 0u, 0u, 0u);
-    }
-}
-
-// Layer l's MMAs for one tile (one elected thread): A from the tile's
-// buffer, B the shared weights; descriptors of K step s are those of step 0
-// with the start address 256 bytes (16 units) further.
-template <int OPS>
-__device__ __forceinline__ void tiny_issue(const TcCfg& tc, int l, uint32_t a_addr, uint32_t w_base, uint32_t tmem,
-                                           uint32_t bar, uint32_t lo_off) {
-    const TcLayer& ly = tc.layer[l];
-    tc_fence_after();
-    const uint32_t sbo = (uint32_t)(ly.Kp >> 3) * 128u;
-    const uint64_t ad = umma_desc(a_addr, 128u, sbo);
-    const uint64_t bd = umma_desc(w_base + ly.w_off, 128u, sbo);
-    const uint64_t bl = bd + (uint64_t)(tc.w_bytes >> 4), al = ad + (uint64_t)(lo_off >> 4);
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        if (s < (ly.Kp >> 4)) {
-            const uint64_t o = (uint64_t)(16 * s);
-            mma_bf16(tmem, ad + o, bd + o, ly.idesc, s > 0 ? 1u : 0u);
-            if (OPS != kOpsBf16) mma_bf16(tmem, ad + o, bl + o, ly.idesc, 1u);
-            if (OPS == kOpsBf16x3) mma_bf16(tmem, al + o, bd + o, ly.idesc, 1u);
-        }
-    }
-    mma_commit(bar);
-}
-
-// ReLU and operand rounding of row t's outputs of a hidden layer (np
-// columns at tmem), written as the next layer's input (32-column layout).
-template <int OPS>
-__device__ __forceinline__ void tiny_convert(uint32_t tmem, int np, uint8_t* sA, uint32_t row32, uint32_t lo_off) {
-#pragma unroll
-    for (int c0 = 0; c0 < 32; c0 += 16) {
-        if (c0 < np) {
-            uint32_t r[16];
-            tmem_ld16(tmem + (uint32_t)c0, r);
-            tmem_wait16(r);
-            uint32_t hi[8], lo[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-                relu_pair<OPS>(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]), hi[i], lo[i]);
-            const uint32_t o = row32 + (uint32_t)(c0 >> 3) * 128u;
-            *reinterpret_cast<uint4*>(sA + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-            *reinterpret_cast<uint4*>(sA + o + 128) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
-            if (OPS == kOpsBf16x3) {
-                *reinterpret_cast<uint4*>(sA + lo_off + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-                *reinterpret_cast<uint4*>(sA + lo_off + o + 128) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
-            }
-        }
-    }
-}
-
-// Decode (Table 1), sample (Sec. 5.3) and density (Eq. 4) of row t of a
-// tile from its 16 raw outputs.
-__device__ __forceinline__ void tiny_decode(const QueryBatch& qb, const TileSeg& ts, int t, const uint32_t (&rawu)[16]) {
-    const QuerySeg& S = *ts.S;
-    const int64_t j = ts.row0 + t, ld = S.ld;
-    const bool valid = j < ts.n;
-    float r[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) r[i] = __uint_as_float(rawu[i]);
-    const float mx = fmaxf(fmaxf(r[0], r[4]), fmaxf(r[8], r[12]));
-    const float2 mxl = f2(-mx * kL2E);
-    const float2 e01 = ex2x2(fma2(make_float2(r[0], r[4]), f2(kL2E), mxl));
-    const float2 e23 = ex2x2(fma2(make_float2(r[8], r[12]), f2(kL2E), mxl));
-    const float ssum = (e01.x + e01.y) + (e23.x + e23.y);  // in [1, 4]
-    const float inv = hw_rcp(ssum);
-    LobePair P0, P1;
-    float* mix = valid ? S.mix : nullptr;
-    decode_pair(mul2(e01, f2(inv)), make_float2(r[1], r[5]), make_float2(r[2], r[6]), make_float2(r[3], r[7]), P0,
-                mix, 0, ld, j);
-    decode_pair(mul2(e23, f2(inv)), make_float2(r[9], r[13]), make_float2(r[10], r[14]), make_float2(r[11], r[15]),
-                P1, mix, 2, ld, j);
-    float w[3] = {0.0f, 0.0f, 1.0f};
-    if (qb.sample) {
-        float u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
-        bool uni = false;
-        if (valid) {
-            u0 = S.uin[j];
-            u1 = S.uin[ld + j];
-            u2 = S.uin[2 * ld + j];
-            uni = S.ufrac > 0.0f && S.uin[3 * ld + j] < S.ufrac;
-        }
-        if (uni) {
-            uniform_sphere(u1, u2, w);
-        } else {
-            // Smallest lobe i with u0 below the running sum of the weights
-            // (the last lobe if rounding leaves u0 above all). The sums are
-            // non-decreasing, so the lobe index is g0 + g1 + g2: the second
-            // pair when g1, the odd lobe of the pair when exactly one or all
-            // three hold.
-            const float c0 = P0.lam.x, c1 = c0 + P0.lam.y, c2 = c1 + P1.lam.x;
-            const bool g0 = u0 >= c0, g1 = u0 >= c1, g2 = u0 >= c2;
-            Lobe sl;
-            const float2 kk = g1 ? P1.kap : P0.kap, xx = g1 ? P1.nx : P0.nx, yy = g1 ? P1.ny : P0.ny,
-                         zz = g1 ? P1.sa : P0.sa;
-            const bool odd = g2 || (g0 && !g1);
-            sl.kap = odd ? kk.y : kk.x;
-            sl.mu[0] = -(odd ? xx.y : xx.x);
-            sl.mu[1] = -(odd ? yy.y : yy.x);
-            sl.mu[2] = -(odd ? zz.y : zz.x);
-            sl.lam = 0.0f;
-            vmf_sample_rp(sl, u1, u2, w);
-        }
-        float pv = pair_pdf(P0, w) + pair_pdf(P1, w);
-        if (S.ufrac > 0.0f) pv = S.ufrac * kInv4Pi + (1.0f - S.ufrac) * pv;
-        if (valid) {
-            S.dir[j] = w[0];
-            S.dir[ld + j] = w[1];
-            S.dir[2 * ld + j] = w[2];
-            S.pdf[j] = pv;
-        }
-    } else {
-        if (valid) {
-            w[0] = S.uin[j];
-            w[1] = S.uin[ld + j];
-            w[2] = S.uin[2 * ld + j];
-        }
-        float pv;
-        if (qb.log_pdf) {
-            const float lnorm = mx + kLn2 * hw_lg2(ssum);
-            const float2 a0 = pair_log_terms(P0, make_float2(r[0], r[4]), lnorm, w);
-            const float2 a1 = pair_log_terms(P1, make_float2(r[8], r[12]), lnorm, w);
-            const float m = fmaxf(fmaxf(a0.x, a0.y), fmaxf(a1.x, a1.y));
-            const float s = __expf(a0.x - m) + __expf(a0.y - m) + __expf(a1.x - m) + __expf(a1.y - m);
-            pv = m + __logf(s);
-        } else {
-            pv = pair_pdf(P0, w) + pair_pdf(P1, w);
-        }
-        if (valid) S.pdf[j] = pv;
-    }
-}
-
-template <int OPS, int G, int P>
-__global__ void __launch_bounds__(kThreads * G, 1) k_forward_tiny(const __grid_constant__ TcCfg tc,
-                                                                  const uint2* __restrict__ grid4,
-                                                                  uint32_t grid_bytes,
-                                                                  const uint8_t* __restrict__ wblob,
-                                                                  const __grid_constant__ QueryBatch qb,
-                                                                  int* __restrict__ status) {
+__global__ void __launch_bounds__(kThreads * kGroups, 1) k_forward_tiny(const __grid_constant__ TcCfg tc,
+                                                                        const uint2* __restrict__ grid4,
+                                                                        uint32_t grid_bytes,
+                                                                        const uint8_t* __restrict__ wblob,
+                                                                        const __grid_constant__ QueryBatch qb,
+                                                                        int* __restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem[];
+    constexpr bool SPLIT = OPS == kOpsBf16x3;
     constexpr int nw = OPS == kOpsBf16 ? 1 : 2;  // weight blobs (hi, residual)
-    constexpr int NS = G * P;                    // tile slots of the CTA
-    const TinyLayout lay = tiny_layout(tc, grid_bytes, G, P);
+    const TinyLayout lay = tiny_layout(tc, grid_bytes);
     const int g = threadIdx.x >> 7;      // tile group
-    const int t = threadIdx.x & 127;     // row of the group's tiles
+    const int t = threadIdx.x & 127;     // row of the group's tile
     const int warp = t >> 5;             // warp within the group (its TMEM lane quarter)
     uint8_t* sW = smem;
     const uint2* sG = reinterpret_cast<const uint2*>(smem + lay.grid);
+    uint8_t* sA = smem + lay.a + (uint32_t)g * lay.a_stride;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + lay.bars);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 1 + NS);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 1 + kGroups);
     const uint32_t bar_w = smem_u32(&bars[0]);
+    const uint32_t bar_mma = smem_u32(&bars[1 + g]);
 
     if (threadIdx.x < 32) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"(32u * NS)
+                     "r"(32u * kGroups)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x == 0) {
-        for (int i = 0; i <= NS; ++i) mbar_init(smem_u32(&bars[i]), 1);
+        for (int i = 0; i <= kGroups; ++i) mbar_init(smem_u32(&bars[i]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem_base = *tslot;
+    // This group's 32 tensor-memory columns.
+    const uint32_t tmem = *tslot + 32u * (uint32_t)g;
     if (threadIdx.x == 0) {
         // Weights and grid table: two bulk copies on one barrier.
         const uint32_t wb = (uint32_t)nw * tc.w_bytes;
@@ -494,23 +303,16 @@ __global__ void __launch_bounds__(kThreads * G, 1) k_forward_tiny(const __grid_c
             : "memory");
     }
     bool ok = !__syncthreads_or(threadIdx.x < 32 && !mbar_wait_bounded(bar_w, 0));
-    // Slot p of this group: activation buffer, 32 TMEM columns and MMA
-    // barrier (addresses formed at use); phase bit p: the barrier's phase;
-    // pend bit p: an MMA batch of the slot not yet waited for.
-    auto sAp = [&](int p) { return smem + lay.a + (uint32_t)(g * P + p) * lay.a_stride; };
-    auto tmp = [&](int p) { return tmem_base + 32u * (uint32_t)(g * P + p); };
-    const uint32_t bar0 = smem_u32(&bars[1 + g * P]);
-    auto barp = [&](int p) { return bar0 + 8u * (uint32_t)p; };
-    uint32_t phase = 0, pend = 0;
+    uint32_t phase = 0;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     // This thread's row in the K-major activation tile: 16-column layout
     // (layer 0) and 32-column layout (layers 1 and 2); chunk c of 8 columns
     // is 128 bytes further.
     const uint32_t row16 = (uint32_t)((t >> 3) * 256 + (t & 7) * 16);
     const uint32_t row32 = (uint32_t)((t >> 3) * 512 + (t & 7) * 16);
-    const uint32_t lo_off = OPS == kOpsBf16x3 ? tc.a_bytes : 0u;
-    const uint32_t D = (uint32_t)tc.base.level_res[0];
-    const uint32_t sW_addr = smem_u32(sW);
+    const uint32_t lo_off = SPLIT ? tc.a_bytes : 0u;
+    const int D = tc.base.level_res[0];
+    const uint32_t uD = (uint32_t)D, uD2 = uD * uD;
     const int np0 = tc.layer[0].Np, np1 = tc.layer[1].Np;
 
     int64_t ntiles = qb.total_tiles, n0 = qb.seg[0].n;
@@ -518,144 +320,256 @@ __global__ void __launch_bounds__(kThreads * G, 1) k_forward_tiny(const __grid_c
         n0 = *qb.n_dev;
         ntiles = (n0 + kTile - 1) / kTile;
     }
-    const int64_t stride = (int64_t)gridDim.x * G;
-    // Waits for slot p's MMA batch (warp 0 of the group on the mbarrier, the
-    // others in the group's barrier, which also passes the outcome on).
-    auto wait_slot = [&](int p) {
-        const bool done = warp != 0 || mbar_wait_bounded(barp(p), (phase >> p) & 1u);
-        ok = !group_sync_or(g, !done);
-        if (ok) {
-            phase ^= 1u << p;
-            pend &= ~(1u << p);
+    const int64_t stride = (int64_t)gridDim.x * kGroups;
+    for (int64_t tile = (int64_t)blockIdx.x * kGroups + g; ok && tile < ntiles; tile += stride) {
+        int sg = 0;
+        while (sg + 1 < qb.nseg && tile >= qb.seg[sg + 1].tile0) ++sg;
+        const QuerySeg& S = qb.seg[sg];
+        const int64_t n = (sg == 0 && qb.n_dev) ? n0 : S.n;
+        const int64_t ld = S.ld;
+        const int64_t j = (tile - S.tile0) * kTile + t;
+        const bool valid = j < n;
+        if (warp == 3) {
+            // Into L2 while this tile is encoded and run through the MLP: its
+            // uniforms (or directions) and the group's next tile's positions.
+            const int lane = t & 31, r = lane >> 2;
+            const int64_t b0 = (tile - S.tile0) * kTile + 32 * (lane & 3);
+            if (r < 4) {
+                if ((r < 3 || S.ufrac > 0.0f) && b0 < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(S.uin + r * ld + b0));
+            } else if (r < 7) {
+                const int64_t nt = tile + stride;
+                if (nt < ntiles) {
+                    int s2 = sg;
+                    while (s2 + 1 < qb.nseg && nt >= qb.seg[s2 + 1].tile0) ++s2;
+                    const QuerySeg& S2 = qb.seg[s2];
+                    const int64_t b2 = (nt - S2.tile0) * kTile + 32 * (lane & 3);
+                    const int64_t n2 = (s2 == 0 && qb.n_dev) ? n0 : S2.n;
+                    if (b2 < n2) asm volatile("prefetch.global.L2 [%0];" ::"l"(S2.pos + (r - 4) * S2.ld + b2));
+                }
+            }
         }
-        return ok;
-    };
-    for (int64_t base = (int64_t)blockIdx.x * G + g; ok && base < ntiles; base += stride * P) {
-        // Layer 0 of every slot's tile, each issued as soon as it is encoded.
+        // ---- encode (Sec. 5.1, Eq. 11): the 8 corners of the cell from the
+        // shared-memory table, blended in FP32, written as this row's first
+        // 8-column chunk (4 features, 4 zeros); the second chunk of the
+        // 16-column input is zero.
+        {
+            float x = 0.0f, y = 0.0f, z = 0.0f;
+            if (valid) {
+                x = S.pos[j];
+                y = S.pos[ld + j];
+                z = S.pos[2 * ld + j];
+            }
+            const Cell cl = make_cell(x, y, z, D);
+            // Corners (x, x + 1) are adjacent entries: four row addresses,
+            // the x-neighbour one entry on.
+            // (the last corner, b + D^2 + D + 1, is below D^3 by the cell clamp)
+            const uint2* r00 = sG + bounded_index(cl.c[0] + uD * (cl.c[1] + uD * cl.c[2]), uD2 * uD - uD2 - uD - 1u);
+            const uint2* rows[4] = {r00, r00 + uD, r00 + uD2, r00 + uD2 + uD};
+            uint2 raw[8];
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const int64_t tile = base + p * stride;
-            if (tile < ntiles) {
-                const TileSeg ts = tile_seg(qb, tile, n0);
-                if (warp == 3) {
-                    // Into L2 while this tile runs through the MLP: its
-                    // uniforms (or directions) and the slot's next positions.
-                    const int lane = t & 31, r = lane >> 2;
-                    const QuerySeg& S = *ts.S;
-                    const int64_t b0 = ts.row0 + 32 * (lane & 3);
-                    if (r < 4) {
-                        if ((r < 3 || S.ufrac > 0.0f) && b0 < ts.n)
-                            asm volatile("prefetch.global.L2 [%0];" ::"l"(S.uin + r * S.ld + b0));
-                    } else if (r < 7) {
-                        const int64_t nt = tile + stride * P;
-                        if (nt < ntiles) {
-                            const TileSeg tn = tile_seg(qb, nt, n0);
-                            const int64_t b2 = tn.row0 + 32 * (lane & 3);
-                            if (b2 < tn.n)
-                                asm volatile("prefetch.global.L2 [%0];" ::"l"(tn.S->pos + (r - 4) * tn.S->ld + b2));
+            for (int c = 0; c < 8; ++c) raw[c] = rows[c >> 1][c & 1];
+            float w8[8];
+            corner_w8(cl, w8);
+            float2 a01 = make_float2(0.0f, 0.0f), a23 = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float2 v01 = __half22float2(*reinterpret_cast<const __half2*>(&raw[c].x));
+                const float2 v23 = __half22float2(*reinterpret_cast<const __half2*>(&raw[c].y));
+                a01 = fma2(f2(w8[c]), v01, a01);
+                a23 = fma2(f2(w8[c]), v23, a23);
+            }
+            uint32_t h01, h23, l01 = 0u, l23 = 0u;
+            feat_pair<OPS>(a01.x, a01.y, h01, l01);
+            feat_pair<OPS>(a23.x, a23.y, h23, l23);
+            *reinterpret_cast<uint4*>(sA + row16) = make_uint4(h01, h23, 0u, 0u);
+            *reinterpret_cast<uint4*>(sA + row16 + 128) = make_uint4(0u, 0u, 0u, 0u);
+            if (SPLIT) {
+                *reinterpret_cast<uint4*>(sA + lo_off + row16) = make_uint4(l01, l23, 0u, 0u);
+                *reinterpret_cast<uint4*>(sA + lo_off + row16 + 128) = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        group_sync(g);
+        uint32_t rawu[16];
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            const TcLayer& ly = tc.layer[l];
+            if (t == 0) {
+                tc_fence_after();
+                // Descriptors of K step s are those of step 0 with the start
+                // address 256 bytes (16 units) further.
+                const uint64_t ad = umma_desc(smem_u32(sA), 128u, (uint32_t)(ly.Kp >> 3) * 128u);
+                const uint64_t bd = umma_desc(smem_u32(sW) + ly.w_off, 128u, (uint32_t)(ly.Kp >> 3) * 128u);
+                const uint64_t bl = bd + (uint64_t)(tc.w_bytes >> 4), al = ad + (uint64_t)(lo_off >> 4);
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    if (s < (ly.Kp >> 4)) {
+                        const uint64_t o = (uint64_t)(16 * s);
+                        mma_bf16(tmem, ad + o, bd + o, ly.idesc, s > 0 ? 1u : 0u);
+                        if (OPS != kOpsBf16) mma_bf16(tmem, ad + o, bl + o, ly.idesc, 1u);
+                        if (SPLIT) mma_bf16(tmem, al + o, bd + o, ly.idesc, 1u);
+                    }
+                }
+                mma_commit(bar_mma);
+            }
+            // Warp 0 of the group waits on the MMA barrier; the group's other
+            // warps wait in its named barrier, which also passes the outcome.
+            const bool done = warp != 0 || mbar_wait_bounded(bar_mma, phase);
+            phase ^= 1u;
+            ok = !group_sync_or(g, !done);
+            if (!ok) break;
+            tc_fence_after();
+            if (l < 2) {
+                // ReLU, BF16 high part and residual of this row's outputs,
+                // as the next layer's input (32-column layout).
+                const int np = l == 0 ? np0 : np1;
+#pragma unroll
+                for (int c0 = 0; c0 < 32; c0 += 16) {
+                    if (c0 < np) {
+                        uint32_t r[16];
+                        tmem_ld16(tmem + lane_base + (uint32_t)c0, r);
+                        tmem_wait16(r);
+                        uint32_t hi[8], lo[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            relu_pair<OPS>(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]), hi[i], lo[i]);
+                        const uint32_t o = row32 + (uint32_t)(c0 >> 3) * 128u;
+                        *reinterpret_cast<uint4*>(sA + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                        *reinterpret_cast<uint4*>(sA + o + 128) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+                        if (SPLIT) {
+                            *reinterpret_cast<uint4*>(sA + lo_off + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                            *reinterpret_cast<uint4*>(sA + lo_off + o + 128) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
                         }
                     }
                 }
-                tiny_encode<OPS>(ts, t, sG, D, sAp(p), row16, lo_off);
                 fence_async_smem();
                 tc_fence_before();
                 group_sync(g);
-                if (t == 0) tiny_issue<OPS>(tc, 0, smem_u32(sAp(p)), sW_addr, tmp(p), barp(p), lo_off);
-                pend |= 1u << p;
-            }
-        }
-        // Layers 1 and 2: each slot's outputs converted and its next layer
-        // issued while the other slots' MMAs run.
-#pragma unroll
-        for (int l = 0; l < 2; ++l) {
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                if (ok && base + p * stride < ntiles) {
-                    if (!wait_slot(p)) break;
-                    tc_fence_after();
-                    tiny_convert<OPS>(tmp(p) + lane_base, l == 0 ? np0 : np1, sAp(p), row32, lo_off);
-                    fence_async_smem();
-                    tc_fence_before();
-                    group_sync(g);
-                    if (t == 0) tiny_issue<OPS>(tc, l + 1, smem_u32(sAp(p)), sW_addr, tmp(p), barp(p), lo_off);
-                    pend |= 1u << p;
-                }
-            }
-        }
-        // Decode, sample and density of each slot's tile.
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const int64_t tile = base + p * stride;
-            if (ok && tile < ntiles) {
-                if (!wait_slot(p)) break;
-                tc_fence_after();
-                uint32_t rawu[16];
-                tmem_ld16(tmp(p) + lane_base, rawu);
+            } else {
+                tmem_ld16(tmem + lane_base, rawu);
                 tmem_wait16(rawu);
                 tc_fence_before();
-                tiny_decode(qb, tile_seg(qb, tile, n0), t, rawu);
             }
+        }
+        if (!ok) break;
+        // ---- decode (Table 1), sample (Sec. 5.3) and density (Eq. 4).
+        float r[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) r[i] = __uint_as_float(rawu[i]);
+        const float mx = fmaxf(fmaxf(r[0], r[4]), fmaxf(r[8], r[12]));
+        const float2 mxl = f2(-mx * kL2E);
+        const float2 e01 = ex2x2(fma2(make_float2(r[0], r[4]), f2(kL2E), mxl));
+        const float2 e23 = ex2x2(fma2(make_float2(r[8], r[12]), f2(kL2E), mxl));
+        const float ssum = (e01.x + e01.y) + (e23.x + e23.y);  // in [1, 4]
+        const float inv = hw_rcp(ssum);
+        LobePair P0, P1;
+        float* mix = valid ? S.mix : nullptr;
+        decode_pair(mul2(e01, f2(inv)), make_float2(r[1], r[5]), make_float2(r[2], r[6]), make_float2(r[3], r[7]),
+                    P0, mix, 0, ld, j);
+        decode_pair(mul2(e23, f2(inv)), make_float2(r[9], r[13]), make_float2(r[10], r[14]),
+                    make_float2(r[11], r[15]), P1, mix, 2, ld, j);
+        float w[3] = {0.0f, 0.0f, 1.0f};
+        const bool sample = qb.sample != 0;
+        if (sample) {
+            float u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
+            bool uni = false;
+            if (valid) {
+                u0 = S.uin[j];
+                u1 = S.uin[ld + j];
+                u2 = S.uin[2 * ld + j];
+                uni = S.ufrac > 0.0f && S.uin[3 * ld + j] < S.ufrac;
+            }
+            if (uni) {
+                uniform_sphere(u1, u2, w);
+            } else {
+                // Smallest lobe i with u0 below the running sum of the
+                // weights (the last lobe if rounding leaves u0 above all).
+                const float c0 = P0.lam.x, c1 = c0 + P0.lam.y, c2 = c1 + P1.lam.x;
+                // The sums are non-decreasing, so the lobe index is
+                // g0 + g1 + g2: the second pair when g1, the odd lobe of the
+                // pair when exactly one or all three hold.
+                const bool g0 = u0 >= c0, g1 = u0 >= c1, g2 = u0 >= c2;
+                Lobe sl;
+                const float2 kk = g1 ? P1.kap : P0.kap, xx = g1 ? P1.nx : P0.nx, yy = g1 ? P1.ny : P0.ny,
+                             zz = g1 ? P1.sa : P0.sa;
+                const bool odd = g2 || (g0 && !g1);
+                sl.kap = odd ? kk.y : kk.x;
+                sl.mu[0] = -(odd ? xx.y : xx.x);
+                sl.mu[1] = -(odd ? yy.y : yy.x);
+                sl.mu[2] = -(odd ? zz.y : zz.x);
+                sl.lam = 0.0f;
+                vmf_sample_rp(sl, u1, u2, w);
+            }
+            float pv = pair_pdf(P0, w) + pair_pdf(P1, w);
+            if (S.ufrac > 0.0f) pv = S.ufrac * kInv4Pi + (1.0f - S.ufrac) * pv;
+            if (valid) {
+                S.dir[j] = w[0];
+                S.dir[ld + j] = w[1];
+                S.dir[2 * ld + j] = w[2];
+                S.pdf[j] = pv;
+            }
+        } else {
+            if (valid) {
+                w[0] = S.uin[j];
+                w[1] = S.uin[ld + j];
+                w[2] = S.uin[2 * ld + j];
+            }
+            float pv;
+            if (qb.log_pdf) {
+                const float lnorm = mx + kLn2 * hw_lg2(ssum);
+                const float2 a0 = pair_log_terms(P0, make_float2(r[0], r[4]), lnorm, w);
+                const float2 a1 = pair_log_terms(P1, make_float2(r[8], r[12]), lnorm, w);
+                const float m = fmaxf(fmaxf(a0.x, a0.y), fmaxf(a1.x, a1.y));
+                const float s = __expf(a0.x - m) + __expf(a0.y - m) + __expf(a1.x - m) + __expf(a1.y - m);
+                pv = m + __logf(s);
+            } else {
+                pv = pair_pdf(P0, w) + pair_pdf(P1, w);
+            }
+            if (valid) S.pdf[j] = pv;
         }
     }
     if (!ok) {
         if (t == 0) atomicOr(status, kStatusTimeout);
         // Drain this group's own asynchronous work (bounded) before the
-        // tensor memory is released: the MMA batches not yet waited for (and,
+        // tensor memory is released: the MMA batch whose wait gave up (and,
         // for group 0, the weights' and grid's bulk copies).
         if (warp == 0) {
             if (g == 0) (void)mbar_wait_bounded(bar_w, 0);
-#pragma unroll
-            for (int p = 0; p < P; ++p)
-                if ((pend >> p) & 1u) (void)mbar_wait_bounded(barp(p), (phase >> p) & 1u);
+            (void)mbar_wait_bounded(bar_mma, phase ^ 1u);
         }
     }
     tc_fence_before();
     __syncthreads();
     if (threadIdx.x < 32) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(32u * NS)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(32u * kGroups)
                      : "memory");
     }
 }
 
 }  // namespace
 
-// Groups and tiles in flight per group of the tiny kernel for an operand
-// format: FP16 and single-pass BF16 keep two tiles per group in eight
-// groups (16 KB of activation tiles per group); split BF16, whose residual
-// tiles double that, keeps one tile in eight groups, or two tiles in four
-// groups (128 registers per thread) with the tuning override NPM_TINY_PIPE=2.
-struct TinyShape {
-    int G, P;
-};
-
-static TinyShape tiny_shape(const TcCfg& c) {
-    if (!c.split) return {8, 2};
-    static std::atomic<int> env_pipe{INT32_MIN + 1};
-    return env_override("NPM_TINY_PIPE", env_pipe) == 2 ? TinyShape{4, 2} : TinyShape{8, 1};
-}
-
 bool tiny_qualifies(const TcCfg& c) {
     const DevCfg& d = c.base;
     const uint32_t grid_bytes = (uint32_t)d.level_res[0] * d.level_res[0] * d.level_res[0] * 8u;
-    const TinyShape sh = tiny_shape(c);
     return d.mode == NPM_RADIANCE && d.n_levels == 1 && d.feat == 4 && (d.dense_mask & 1u) && d.n_layers == 3 &&
            d.K == 4 && d.kappa_act == NPM_SOFTPLUS && c.layer[0].Kp == 16 && c.layer[0].Np <= 32 &&
            c.layer[1].Kp == 32 && c.layer[1].Np <= 32 && c.layer[2].Kp == 32 && c.layer[2].Np == 16 &&
            c.a0_bytes == 0 && c.a_bytes == (uint32_t)(kTile * 32 * 2) && grid_bytes % 16u == 0 &&
-           tiny_layout(c, grid_bytes, sh.G, sh.P).bytes <= 227u * 1024u;
+           tiny_layout(c, grid_bytes).bytes <= 227u * 1024u;
 }
 
-template <int OPS, int G, int P>
-static cudaError_t launch_tiny_inst(const TcCfg& c, const __half* grid_h, const uint8_t* wblob, QueryBatch& qb,
-                                    int64_t max_n, int* status, cudaStream_t st) {
-    auto kern = k_forward_tiny<OPS, G, P>;
+cudaError_t launch_tiny(const TcCfg& c, size_t, const __half* grid_h, const uint8_t* wblob, QueryBatch& qb,
+                        int64_t max_n, int* status, cudaStream_t st) {
+    auto kern = c.split ? k_forward_tiny<kOpsBf16x3> : c.f16 ? k_forward_tiny<kOpsFp16> : k_forward_tiny<kOpsBf16>;
     const uint32_t grid_bytes = (uint32_t)c.base.level_res[0] * c.base.level_res[0] * c.base.level_res[0] * 8u;
-    const size_t smem = tiny_layout(c, grid_bytes, G, P).bytes;
-    // One CTA per SM (G x 128 threads; the register file split between
-    // them); carve out just its shared memory so the rest stays L1.
-    static std::atomic<uint64_t> attrs{~0ull};
-    cudaError_t e = set_smem_attrs(kern, smem, carveout_percent(smem + 1024), attrs);
+    const size_t smem = tiny_layout(c, grid_bytes).bytes;
+    // One CTA per SM (kGroups x 128 threads at 64 registers); carve out just
+    // its shared memory so the rest stays L1.
+    static std::atomic<uint64_t> attrs_s{~0ull}, attrs_h{~0ull}, attrs_p{~0ull};
+    cudaError_t e = set_smem_attrs(kern, smem, carveout_percent(smem + 1024),
+                                   c.split ? attrs_s : c.f16 ? attrs_h : attrs_p);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -667,22 +581,12 @@ static cudaError_t launch_tiny_inst(const TcCfg& c, const __half* grid_h, const 
     }
     qb.total_tiles = t0;
     const int64_t hint = qb.n_dev ? (max_n + kTile - 1) / kTile : t0;
-    int64_t g = (hint + G * P - 1) / (G * P);
+    int64_t g = (hint + kGroups - 1) / kGroups;
     if (g > sms) g = sms;
     if (g < 1) g = 1;
-    kern<<<(int)g, kThreads * G, smem, st>>>(c, reinterpret_cast<const uint2*>(grid_h), grid_bytes, wblob, qb,
-                                              status);
+    kern<<<(int)g, kThreads * kGroups, smem, st>>>(c, reinterpret_cast<const uint2*>(grid_h), grid_bytes, wblob, qb,
+                                                   status);
     return cudaGetLastError();
-}
-
-cudaError_t launch_tiny(const TcCfg& c, size_t, const __half* grid_h, const uint8_t* wblob, QueryBatch& qb,
-                        int64_t max_n, int* status, cudaStream_t st) {
-    if (c.split)
-        return tiny_shape(c).P == 2
-                   ? launch_tiny_inst<kOpsBf16x3, 4, 2>(c, grid_h, wblob, qb, max_n, status, st)
-                   : launch_tiny_inst<kOpsBf16x3, 8, 1>(c, grid_h, wblob, qb, max_n, status, st);
-    if (c.f16) return launch_tiny_inst<kOpsFp16, 8, 2>(c, grid_h, wblob, qb, max_n, status, st);
-    return launch_tiny_inst<kOpsBf16, 8, 2>(c, grid_h, wblob, qb, max_n, status, st);
 }
 
 }  // namespace tc
