@@ -152,6 +152,11 @@ WORKLOADS = {
     "tiny": TINY,
     "paper_hash": PAPER_HASH,
     "tiny_bf16": TINY_BF16,
+    "tiny_fp16": TINY_BF16.with_(
+        name="tiny dense 16^3x4, MLP 4-32-32-16, K=4, fp16 tensor-core MLP / fp16 grid", precision=FP16),
+    # The serving loop's per-frame training batch on the tiny network.
+    "tiny_bf16_train": TINY_BF16.with_(
+        name="tiny dense 16^3x4, MLP 4-32-32-16, K=4, split-bf16, training batch 2^18", n_train=1 << 18),
     "product_bf16": PRODUCT_BF16,
     "paper_own": PAPER_OWN,
     "paper_hash_bf16": PAPER_HASH.with_(
