@@ -609,11 +609,12 @@ def main():
         "value": value, "unit": "samples/s" if train_mode else "queries/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {synth.FP32: "f32", synth.BF16: "bf16", synth.BF16X3: "bf16x3 (split bf16)"}[w.precision],
+        "dtype": {synth.FP32: "f32", synth.BF16: "bf16", synth.BF16X3: "bf16x3 (split bf16)",
+                  synth.FP16: "f16"}[w.precision],
         "data": "synthetic (seeded positions/uniforms; parameters with kappa up to ~35)",
         "config": {"workload": w.name, ("samples_per_step" if train_mode else "queries_per_step"): n,
                    "l2": (f"two training batches alternate ({2 * n * 40 / 1e6:.0f} MB) and every step "
-                          "streams the 167 MB Adam state" if train_mode else
+                          f"streams the {34 * m.num_params() / 1e6:.1f} MB Adam state" if train_mode else
                           f"inputs rotate over {nrot} batches ({nrot * n * 40 / 1e6:.0f} MB incl. outputs) > L2"),
                    "parallelism": f"dp{world} (independent batches per GPU)"},
         "latency": {"p50_ms": per_sorted[len(per) // 2],
