@@ -47,6 +47,15 @@ struct DevCfg {
 // g_bounds_violations and replaced by 0, so the access stays inside the
 // buffer and the kernel carries on (no trap). npm_debug_bounds_violations
 // reads the count. In the normal build the check compiles away.
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while its predecessor in the stream is still
+// running; grid_dep_wait() returns once that predecessor has completed and
+// its writes are visible (at once for a kernel launched without it).
+// grid_dep_launch() lets the stream's next such kernel be scheduled.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 #ifdef NPM_DEBUG_BOUNDS
 extern __device__ unsigned long long g_bounds_violations;
 __device__ __forceinline__ uint32_t bounded_index(uint32_t idx, uint32_t limit) {

@@ -139,6 +139,8 @@ __global__ void k_wf_start(WfState s) {
 // next bounce's destination, which no later kernel reads before the next
 // advance appends to it).
 __global__ void k_wf_stamp(WfState s, int slot, int clear) {
+    npm::grid_dep_wait();
+    npm::grid_dep_launch();
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         stamp(s, slot);
         if (clear >= 0) s.count[clear] = 0;
@@ -156,6 +158,10 @@ static_assert(kAdvanceThreads % 32 == 0 && kAdvanceThreads <= 1024,
 // bounce; each survivor also gets the next bounce's uniforms at its new
 // queue slot (this bounce's query kernel has consumed the old ones).
 __global__ void __launch_bounds__(kAdvanceThreads) k_wf_advance(WfState s, int b, int src) {
+    // Launched as a programmatic dependent of the query kernel: its blocks
+    // may be scheduled early, and read nothing until that kernel completes.
+    npm::grid_dep_wait();
+    npm::grid_dep_launch();
     const uint64_t f = *s.frame;
     const int64_t n = s.count[src];
     const int dst = src ^ 1;
@@ -253,8 +259,14 @@ npm_status enqueue_frame(npm_wavefront* w, cudaStream_t st) {
     WfState& s = w->st;
     npm_handle* h = w->h;
     const int g = grid_for(s.P);
+    // Within a frame the stamp, query and advance kernels of the bounces are
+    // programmatic dependents of their predecessors (each waits for it
+    // before reading its results; the query kernel's prologue and every
+    // launch overlap the previous kernel's tail). None of them writes the
+    // model, which only the training step at the end of the frame updates.
     k_wf_start<<<g, 256, 0, st>>>(s);  // also zeroes count[1]
-    k_wf_stamp<<<1, 32, 0, st>>>(s, 0, -1);
+    cudaError_t le = npm::launch_maybe_pdl(k_wf_stamp, dim3(1), dim3(32), 0, st, true, s, 0, -1);
+    if (le != cudaSuccess) return npm::set_error(NPM_ERR_CUDA, cudaGetErrorString(le));
     for (int b = 0; b < s.bounces; ++b) {
         const int src = b & 1;
         npm::QueryBatch qb;
@@ -270,12 +282,14 @@ npm_status enqueue_frame(npm_wavefront* w, cudaStream_t st) {
         q.dir = s.dir;
         q.pdf = s.pdf;
         q.ufrac = w->cfg.uniform_frac;
-        cudaError_t e = h->tc ? npm::tc_query_batch(h, qb, s.P, st)
+        cudaError_t e = h->tc ? npm::tc_query_batch(h, qb, s.P, st, true)
                               : npm::launch_forward_fp32_batch(h->dc, inf_params(h), inf_wfwd(h), qb, s.P, st, status_word(h), h->wait_limit);
         if (e != cudaSuccess) return npm::set_error(NPM_ERR_CUDA, cudaGetErrorString(e));
-        k_wf_advance<<<g, kAdvanceThreads, 0, st>>>(s, b, src);
+        e = npm::launch_maybe_pdl(k_wf_advance, dim3(g), dim3(kAdvanceThreads), 0, st, true, s, b, src);
+        if (e != cudaSuccess) return npm::set_error(NPM_ERR_CUDA, cudaGetErrorString(e));
         // count[src] was this bounce's queue: the next advance appends to it
-        k_wf_stamp<<<1, 32, 0, st>>>(s, 2 + 2 * b, src);
+        e = npm::launch_maybe_pdl(k_wf_stamp, dim3(1), dim3(32), 0, st, true, s, 2 + 2 * b, src);
+        if (e != cudaSuccess) return npm::set_error(NPM_ERR_CUDA, cudaGetErrorString(e));
     }
     npm_status rs = npm_train_step(h, s.T, s.tpos, nullptr, s.tdir, s.trad, s.tpdf, s.T, w->loss, st);
     if (rs != NPM_OK) return rs;

@@ -79,7 +79,10 @@ npm_status set_error(npm_status s, const char* msg);
 npm_status tc_create(npm_handle* h);
 void tc_destroy(npm_handle* h);
 cudaError_t tc_refresh_weights(npm_handle* h, cudaStream_t st);
-cudaError_t tc_query_batch(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStream_t st);
+// pdl: the small networks' kernel may be launched as a programmatic
+// dependent of the stream's previous kernel, which must then not write the
+// model's weights or grid (other kernels launch as usual).
+cudaError_t tc_query_batch(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStream_t st, bool pdl = false);
 // Training step kernels on tensor cores (split BF16 operands).
 bool tc_can_train(npm_handle* h);
 cudaError_t tc_train(npm_handle* h, int64_t n, int64_t ld, const float* pos, const float* aux, const float* dir,

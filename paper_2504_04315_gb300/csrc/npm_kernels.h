@@ -31,6 +31,26 @@ inline cudaError_t set_smem_attrs(KernelT kern, size_t smem, int carveout_pct, s
     return cudaSuccess;
 }
 
+// Launch of kern<<<grid, block, smem, st>>>(args...), with programmatic
+// stream serialization when pdl is set: the kernel may then be scheduled
+// before the stream's previous kernel completes, and must call
+// grid_dep_wait() before it reads anything that kernel writes.
+template <typename... Params, typename... Args>
+inline cudaError_t launch_maybe_pdl(void (*kern)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                    bool pdl, Args&&... args) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = grid;
+    lc.blockDim = block;
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&lc, kern, static_cast<Args&&>(args)...);
+}
+
 // Integer tuning override from the environment, read once per process
 // (`cache` holds it; INT32_MIN when unset or not a number).
 inline int env_override(const char* name, std::atomic<int>& cache) {

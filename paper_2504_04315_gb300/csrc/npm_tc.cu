@@ -1570,7 +1570,7 @@ cudaError_t tc_train(npm_handle* h, int64_t n, int64_t ld, const float* pos, con
               : launch_train_tc<16, false>(h, n, ld, pos, aux, dir, rad, spdf, dlogv, loss, st);
 }
 
-cudaError_t tc_query_batch(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStream_t st) {
+cudaError_t tc_query_batch(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStream_t st, bool pdl) {
     const int K = h->cfg.K, L = h->cfg.n_layers;
     const bool f2 = h->cfg.feat_per_level == 2;
     // The small serving networks get their own kernel (npm_tc_tiny.cu);
@@ -1578,7 +1578,8 @@ cudaError_t tc_query_batch(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStr
     static std::atomic<int> env_tiny{INT32_MIN + 1};
     if (tiny_qualifies(h->tc->cfg) && env_override("NPM_TC_TINY", env_tiny) != 0) {
         const uint8_t* wb = h->ema ? h->tc->wblob_inf : h->tc->wblob;
-        return launch_tiny(h->tc->cfg, h->tc->smem, h->grid_h, wb, qb, max_n, reinterpret_cast<int*>(h->scalars + 8), st);
+        return launch_tiny(h->tc->cfg, h->tc->smem, h->grid_h, wb, qb, max_n, reinterpret_cast<int*>(h->scalars + 8), st,
+                           pdl);
     }
     // Tuning override NPM_TC_DECODE=1: the warp-per-query decode in the
     // general kernel (built for the four- and eight-lobe instances; it stages

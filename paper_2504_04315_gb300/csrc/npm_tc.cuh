@@ -273,10 +273,13 @@ __device__ __forceinline__ void vmf_sample_rp(const Lobe& L, float u1, float u2,
 // mode, one dense level of 4 features, three layers of at most 32 outputs
 // (padded input 16), K = 4, softplus kappa, layer 0 sharing the activation
 // buffer. launch_tiny takes the general kernel's configuration, shared
-// memory size, FP16 grid and weight blob.
+// memory size, FP16 grid and weight blob. With pdl the kernel is launched as
+// a programmatic dependent of the stream's previous kernel: its prologue
+// (tensor-memory allocation, copies of the weights and grid) overlaps that
+// kernel, which therefore must not write the weights or the grid.
 bool tiny_qualifies(const TcCfg& c);
 cudaError_t launch_tiny(const TcCfg& c, size_t smem, const __half* grid_h, const uint8_t* wblob, QueryBatch& qb,
-                        int64_t max_n, int* status, cudaStream_t st);
+                        int64_t max_n, int* status, cudaStream_t st, bool pdl = false);
 
 }  // namespace tc
 }  // namespace npm

@@ -302,6 +302,12 @@ __global__ void __launch_bounds__(kThreads * kGroups, 1) k_forward_tiny(const __
             "l"(grid4), "r"(grid_bytes), "r"(bar_w)
             : "memory");
     }
+    // Launched as a programmatic dependent (the wavefront frames), the steps
+    // above overlap the previous kernel; the queries and their count are
+    // read only after it has completed. The weights and grid copied above
+    // are not written by that kernel.
+    grid_dep_wait();
+    grid_dep_launch();
     bool ok = !__syncthreads_or(threadIdx.x < 32 && !mbar_wait_bounded(bar_w, 0));
     uint32_t phase = 0;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
@@ -561,7 +567,7 @@ bool tiny_qualifies(const TcCfg& c) {
 }
 
 cudaError_t launch_tiny(const TcCfg& c, size_t, const __half* grid_h, const uint8_t* wblob, QueryBatch& qb,
-                        int64_t max_n, int* status, cudaStream_t st) {
+                        int64_t max_n, int* status, cudaStream_t st, bool pdl) {
     auto kern = c.split ? k_forward_tiny<kOpsBf16x3> : c.f16 ? k_forward_tiny<kOpsFp16> : k_forward_tiny<kOpsBf16>;
     const uint32_t grid_bytes = (uint32_t)c.base.level_res[0] * c.base.level_res[0] * c.base.level_res[0] * 8u;
     const size_t smem = tiny_layout(c, grid_bytes).bytes;
@@ -584,9 +590,8 @@ cudaError_t launch_tiny(const TcCfg& c, size_t, const __half* grid_h, const uint
     int64_t g = (hint + kGroups - 1) / kGroups;
     if (g > sms) g = sms;
     if (g < 1) g = 1;
-    kern<<<(int)g, kThreads * kGroups, smem, st>>>(c, reinterpret_cast<const uint2*>(grid_h), grid_bytes, wblob, qb,
-                                                   status);
-    return cudaGetLastError();
+    return launch_maybe_pdl(kern, dim3((unsigned)g), dim3(kThreads * kGroups), smem, st, pdl, c,
+                            reinterpret_cast<const uint2*>(grid_h), grid_bytes, wblob, qb, status);
 }
 
 }  // namespace tc
