@@ -737,8 +737,8 @@ __global__ void k_tc_weights(TcCfg tc, const float* __restrict__ mlp, uint8_t* _
 // ----------------------------------------------------------- training
 
 // Training layout: per layer the input activation tile H_l (BF16, K-major,
-// 128 x Kp_l) at h_off, the delta tile D (BF16, K-major, 128 x 128) at
-// d_off; TMEM columns [0, c0) hold the forward / input-gradient
+// 128 x Kp_l) at h_off, the delta tile D (BF16, K-major, 128 samples x
+// d_cols, the widest layer) at d_off; TMEM columns [0, c0) hold the forward / input-gradient
 // accumulator and [dw_col_l, dw_col_l + Kp_l) the weight gradient of
 // layer l, accumulated over all tiles of the CTA.
 struct TcTrain {
@@ -747,6 +747,7 @@ struct TcTrain {
     uint32_t idesc_dw[NPM_MAX_LAYERS];  // A MN-major, B MN-major, N = Kp_l
     uint32_t idesc_dx[NPM_MAX_LAYERS];  // A K-major,  B MN-major, N = Kp_l
     uint32_t d_off, x_off, bar_off, smem, tmem_cols;
+    uint32_t d_cols;                    // columns of the delta tile
     int64_t woff[NPM_MAX_LAYERS];       // packed offset of W_l in the MLP region
     int split;                          // BF16 residual operands (three MMAs per K step)
     uint32_t hlo_off;                   // residual of the current layer's input tile
@@ -950,10 +951,11 @@ __global__ void __launch_bounds__(256) k_train_encode(const __grid_constant__ De
     }
 }
 
-// The small four-lobe instance (single-level grids) is compiled for two
-// CTAs per SM (it fits 128 registers without spills): its tile chain of MMA
-// round trips is latency-bound, and a second CTA overlaps it.
-__host__ __device__ constexpr int train_ctas_per_sm(int kmax, bool f2) { return (kmax == 4 && !f2) ? 2 : 1; }
+// The small four-lobe instance (single-level grids) is compiled for three
+// CTAs per SM (it fits 80 registers without spills, and its delta tiles are
+// only as wide as its layers): its tile chain of MMA round trips is
+// latency-bound, and the other CTAs overlap it.
+__host__ __device__ constexpr int train_ctas_per_sm(int kmax, bool f2) { return (kmax == 4 && !f2) ? 3 : 1; }
 
 template <int KMAX, bool F2>
 __global__ void __launch_bounds__(kTrainThreads, train_ctas_per_sm(KMAX, F2)) k_train_tc(
@@ -1003,6 +1005,7 @@ __global__ void __launch_bounds__(kTrainThreads, train_ctas_per_sm(KMAX, F2)) k_
     const uint32_t sW_addr = smem_u32(sW), sD_addr = smem_u32(sD), base_addr = smem_u32(smem);
     const uint32_t wlo = tc.w_bytes;                      // residual weights follow the high parts
     const uint32_t hlo_addr = base_addr + tt.hlo_off, dlo_addr = base_addr + tt.dlo_off;
+    const uint32_t drg = tt.d_cols * 16u;  // bytes per 8-sample row group of the delta tile
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     // Grid levels of this half: [lv0, lv1); the second half also encodes the
     // product-mode inputs and the padding.
@@ -1142,7 +1145,7 @@ __global__ void __launch_bounds__(kTrainThreads, train_ctas_per_sm(KMAX, F2)) k_
         float dr[4 * KH];
         gh.pass2(lse, lsa, sc, dr);
         const uint32_t dlo = tt.split ? tt.dlo_off - tt.d_off : 0u;
-        store_cols<4 * KH>(sD, row, half * 4 * KH, 128, dr, dlo);
+        store_cols<4 * KH>(sD, row, half * 4 * KH, (int)tt.d_cols, dr, dlo);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -1155,21 +1158,21 @@ __global__ void __launch_bounds__(kTrainThreads, train_ctas_per_sm(KMAX, F2)) k_
                 // dW_l += D^T H_l: M = 128 (outputs), N = Kp_l, K = 128 samples.
                 for (int s = 0; s < 8; ++s) {
                     const uint64_t bh = umma_desc(base_addr + tt.h_off[l] + s * 2u * hk, hk, 128u);
-                    mma_bf16(tmem + tt.dw_col[l], umma_desc(sD_addr + s * 2u * 2048u, 2048u, 128u), bh,
+                    mma_bf16(tmem + tt.dw_col[l], umma_desc(sD_addr + s * 2u * drg, drg, 128u), bh,
                              tt.idesc_dw[l], (first && s == 0) ? 0u : 1u);
                     if (tt.split)
-                        mma_bf16(tmem + tt.dw_col[l], umma_desc(dlo_addr + s * 2u * 2048u, 2048u, 128u), bh,
+                        mma_bf16(tmem + tt.dw_col[l], umma_desc(dlo_addr + s * 2u * drg, drg, 128u), bh,
                                  tt.idesc_dw[l], 1u);
                 }
                 // D W_l: M = 128 samples, N = Kp_l, K = Np_l outputs.
                 for (int s = 0; s < (ly.Np >> 4); ++s) {
-                    const uint64_t ad = umma_desc(sD_addr + s * 256u, 128u, 2048u);
+                    const uint64_t ad = umma_desc(sD_addr + s * 256u, 128u, drg);
                     const uint64_t bd = umma_desc(sW_addr + ly.w_off + s * 2u * hk, hk, 128u);
                     mma_bf16(tmem, ad, bd, tt.idesc_dx[l], s > 0 ? 1u : 0u);
                     if (tt.split) {
                         mma_bf16(tmem, ad, umma_desc(sW_addr + wlo + ly.w_off + s * 2u * hk, hk, 128u),
                                  tt.idesc_dx[l], 1u);
-                        mma_bf16(tmem, umma_desc(dlo_addr + s * 256u, 128u, 2048u), bd, tt.idesc_dx[l], 1u);
+                        mma_bf16(tmem, umma_desc(dlo_addr + s * 256u, 128u, drg), bd, tt.idesc_dx[l], 1u);
                     }
                 }
                 mma_commit(bar_mma);
@@ -1197,7 +1200,7 @@ __global__ void __launch_bounds__(kTrainThreads, train_ctas_per_sm(KMAX, F2)) k_
                         v[2 * i] = hv.x > 0.0f ? __uint_as_float(r[2 * i]) : 0.0f;
                         v[2 * i + 1] = hv.y > 0.0f ? __uint_as_float(r[2 * i + 1]) : 0.0f;
                     }
-                    store16(sD, tile_off(row, c0, 128), tile_off(row, c0 + 8, 128), v, dlo);
+                    store16(sD, tile_off(row, c0, (int)tt.d_cols), tile_off(row, c0 + 8, (int)tt.d_cols), v, dlo);
                 }
                 fence_async_smem();
                 tc_fence_before();
@@ -1403,10 +1406,21 @@ npm_status tc_create(npm_handle* h) {
         uint32_t pw = 32;
         while (pw < cols) pw <<= 1;
         tr.tmem_cols = pw;
+        // Delta tile: as wide as the widest layer (inputs or outputs). The
+        // weight-gradient MMA reads it transposed with M = 128 output rows:
+        // rows beyond the layer's outputs come from the next row groups and,
+        // past the last one, up to 2 KB beyond the tile (the residual tile
+        // and the exchange buffer that follow); they land in weight-gradient
+        // rows that are never read.
+        uint32_t dcols = 16;
+        for (int l = 0; l < c.n_layers; ++l)
+            dcols = std::max<uint32_t>(dcols, (uint32_t)std::max(t.layer[l].Kp, t.layer[l].Np));
+        tr.d_cols = dcols;
         tr.d_off = (off + 127u) / 128u * 128u;
-        tr.dlo_off = tr.d_off + kTile * 128 * 2;
-        tr.x_off = tr.dlo_off + (tr.split ? kTile * 128 * 2 : 0);
+        tr.dlo_off = tr.d_off + kTile * dcols * 2;
+        tr.x_off = tr.dlo_off + (tr.split ? kTile * dcols * 2 : 0);
         tr.bar_off = tr.x_off + 2 * kTile * 16;
+        static_assert(2 * kTile * 16 >= 2048, "the exchange buffer covers the delta tile's over-read");
         tr.smem = tr.bar_off + 64;
         s->can_train = fits && pw <= 512 && tr.smem <= 220 * 1024;
     }
