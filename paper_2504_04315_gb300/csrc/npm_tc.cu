@@ -1060,6 +1060,15 @@ __global__ void __launch_bounds__(kTrainThreads, train_ctas_per_sm(KMAX, F2)) k_
             tc_encode<F2>(tc, grid32, j, valid, ld, pos, aux, smem + tt.h_off[0], row, tc.split ? tc.a_bytes : 0u,
                           true, lv0, lv1, half == 1);
         }
+        // The loss inputs of this row, loaded now so that their latency
+        // passes during the forward layers' tensor-core round trips.
+        float w[3] = {0.0f, 0.0f, 1.0f}, sc = 0.0f;
+        if (valid) {
+            w[0] = dir[j];
+            w[1] = dir[ld + j];
+            w[2] = dir[2 * ld + j];
+            sc = dlogv ? dlogv[j] : -(rad[j] / spdf[j]) * inv_n;
+        }
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -1127,13 +1136,6 @@ __global__ void __launch_bounds__(kTrainThreads, train_ctas_per_sm(KMAX, F2)) k_
         }
         if (!ok) break;
         // Loss and d loss / d raw (zero for rows beyond n).
-        float w[3] = {0.0f, 0.0f, 1.0f}, sc = 0.0f;
-        if (valid) {
-            w[0] = dir[j];
-            w[1] = dir[ld + j];
-            w[2] = dir[2 * ld + j];
-            sc = dlogv ? dlogv[j] : -(rad[j] / spdf[j]) * inv_n;
-        }
         GradHalf<KMAX> gh;
         const float4 part = gh.pass1(cfg, half, raw, w);
         xch[half * kTile + row] = part;
