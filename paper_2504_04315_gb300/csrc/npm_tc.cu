@@ -1041,19 +1041,31 @@ __global__ void __launch_bounds__(kTrainThreads, train_ctas_per_sm(KMAX, F2)) k_
         }
     };
     const int64_t ntiles = (n + kTile - 1) / kTile;
+    // This half's grid features (two per level, at most 8 levels) of row
+    // `row` of tile tl from k_train_encode, loaded one tile ahead.
+    float2 ev[8];
+    auto load_enc = [&](int64_t tl) {
+        const int64_t jj = tl * kTile + row;
+        const bool v = tl < ntiles && jj < n;
+        const float* er = enc + (v ? jj : 0) * (int64_t)cfg.grid_feats;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            ev[q] = (v && lv0 + q < lv1) ? __ldg(reinterpret_cast<const float2*>(er + 2 * (lv0 + q)))
+                                         : make_float2(0.0f, 0.0f);
+    };
+    if (F2 && enc) load_enc(blockIdx.x);
     for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
         const int64_t j = tile * kTile + row;
         const bool valid = j < n;
         if (F2 && enc) {
-            // This half's grid features from k_train_encode (two per level),
-            // then the product-mode inputs and the padding.
+            // This half's grid features, then the product-mode inputs and
+            // the padding; the next tile's features are loaded meanwhile.
             const int kp0 = tc.layer[0].Kp;
             const uint32_t lo = tc.split ? tc.a_bytes : 0u;
-            const float* er = enc + (valid ? j : 0) * (int64_t)cfg.grid_feats;
-            for (int l = lv0; l < lv1; ++l) {
-                const float2 v = valid ? __ldg(reinterpret_cast<const float2*>(er + 2 * l)) : make_float2(0.0f, 0.0f);
-                store_pair(smem + tt.h_off[0], tile_off(row, 2 * l, kp0), v.x, v.y, lo);
-            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (lv0 + q < lv1) store_pair(smem + tt.h_off[0], tile_off(row, 2 * (lv0 + q), kp0), ev[q].x, ev[q].y, lo);
+            load_enc(tile + gridDim.x);
             tc_encode<F2>(tc, grid32, j, valid, ld, pos, aux, smem + tt.h_off[0], row, lo, true, lv1, lv1,
                           half == 1);
         } else {
