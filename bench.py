@@ -610,7 +610,7 @@ def main():
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
         "dtype": {synth.FP32: "f32", synth.BF16: "bf16", synth.BF16X3: "bf16x3 (split bf16)",
-                  synth.FP16: "f16"}[w.precision],
+                  synth.FP16: "f16", synth.FP32_TC: "f16x2 split (FP32 accuracy)"}[w.precision],
         "data": "synthetic (seeded positions/uniforms; parameters with kappa up to ~35)",
         "config": {"workload": w.name, ("samples_per_step" if train_mode else "queries_per_step"): n,
                    "l2": (f"two training batches alternate ({2 * n * 40 / 1e6:.0f} MB) and every step "

@@ -70,7 +70,7 @@ typedef enum {
 
 enum { NPM_RADIANCE = 0, NPM_PRODUCT = 1 };  /* Sec. 4.1 / Sec. 4.3 */
 enum { NPM_SOFTPLUS = 0, NPM_EXP = 1 };      /* kappa mapping; Table 1 uses exp */
-enum { NPM_FP32 = 0, NPM_BF16 = 1, NPM_BF16X3 = 2, NPM_FP16 = 3 };  /* MLP / grid arithmetic */
+enum { NPM_FP32 = 0, NPM_BF16 = 1, NPM_BF16X3 = 2, NPM_FP16 = 3, NPM_FP32_TC = 4 };  /* MLP / grid arithmetic */
 
 #define NPM_MAX_LEVELS 32
 #define NPM_MAX_LAYERS 8
@@ -107,8 +107,19 @@ enum { NPM_FP32 = 0, NPM_BF16 = 1, NPM_BF16X3 = 2, NPM_FP16 = 3 };  /* MLP / gri
  *                  residual (two MMAs per K step); vMF math in FP32. Meets
  *                  the bar (the FP16 rounding of the activations puts the
  *                  density within about 5e-3 at the 99.9th percentile).
+ *                  NPM_FP32_TC: the FP32 path's accuracy on tensor cores:
+ *                  the FP32 grid table, and every activation and weight
+ *                  split into an FP16 high part and an FP16 residual (about
+ *                  22 significant bits), each product hi*hi + hi*lo + lo*hi
+ *                  (three MMAs per K step) with FP32 accumulation; vMF math
+ *                  and sampling as in NPM_FP32. Held to the FP32 bars
+ *                  (density and direction within 1e-4). Values beyond the
+ *                  FP16 range (|v| > 65504) saturate; below |v| = 0.125 the
+ *                  residual is an FP16 subnormal, so such values are held
+ *                  to an absolute error of 2^-25 rather than 22 bits.
+ *                  Training in this mode runs the FP32 kernels.
  *                  Training (npm_train_step, npm_backward) multiplies split
- *                  operands in both reduced-precision modes. Master
+ *                  BF16 operands in the reduced-precision modes. Master
  *                  parameters and Adam state are FP32 in all modes.
  *   lr, beta1, beta2, eps   Adam (Sec. 5.3 uses lr 0.005).
  *   max_batch      largest n of any call; sizes the workspace.

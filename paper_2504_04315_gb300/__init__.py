@@ -17,7 +17,7 @@ from ._lib import NpmError  # noqa: F401
 
 RADIANCE, PRODUCT = 0, 1
 SOFTPLUS, EXP = 0, 1
-FP32, BF16, BF16X3, FP16 = 0, 1, 2, 3
+FP32, BF16, BF16X3, FP16, FP32_TC = 0, 1, 2, 3, 4
 
 
 def _torch():

@@ -115,8 +115,9 @@ npm_status validate(const npm_config* c) {
     if (c->kappa_act != NPM_SOFTPLUS && c->kappa_act != NPM_EXP)
         return fail(NPM_ERR_INVALID_ARG, "kappa_act must be NPM_SOFTPLUS or NPM_EXP");
     if (c->precision != NPM_FP32 && c->precision != NPM_BF16 && c->precision != NPM_BF16X3 &&
-        c->precision != NPM_FP16)
-        return fail(NPM_ERR_INVALID_ARG, "precision must be NPM_FP32, NPM_BF16, NPM_BF16X3 or NPM_FP16");
+        c->precision != NPM_FP16 && c->precision != NPM_FP32_TC)
+        return fail(NPM_ERR_INVALID_ARG,
+                    "precision must be NPM_FP32, NPM_BF16, NPM_BF16X3, NPM_FP16 or NPM_FP32_TC");
     if (c->max_batch < 0 || c->max_batch > ((int64_t)1 << 31))
         return fail(NPM_ERR_INVALID_ARG, "max_batch out of range [0, 2^31]");
     if (!(c->lr >= 0.0f) || !(c->beta1 >= 0.0f && c->beta1 < 1.0f) ||

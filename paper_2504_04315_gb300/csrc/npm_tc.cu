@@ -24,6 +24,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "npm_handle.h"
 #include "npm_kernels.h"
@@ -136,7 +137,7 @@ __device__ __forceinline__ void tc_encode(const TcCfg& tc, const GT* __restrict_
         for (int i = 0; i < 4; ++i) {
             if (f16) {
                 hw[i] = pack_f16_sat(e[2 * i], e[2 * i + 1]);
-                lw[i] = 0u;
+                lw[i] = lo ? f16_residual(hw[i], e[2 * i], e[2 * i + 1]) : 0u;
             } else {
                 __nv_bfloat162 hb = __floats2bfloat162_rn(e[2 * i], e[2 * i + 1]);
                 hw[i] = *reinterpret_cast<uint32_t*>(&hb);
@@ -333,7 +334,8 @@ __device__ __forceinline__ void tc_decode(const TcCfg& tc, const float (&raw)[4 
 #pragma unroll
             for (int i = 1; i < KMAX; ++i)
                 if (i == sel) sl = lob[i];
-            vmf_sample_rp(sl, u1, u2, w);
+            if (tc.fp32) vmf_sample(sl, u1, u2, w);  // the FP32 path's sampler
+            else vmf_sample_rp(sl, u1, u2, w);
         }
     } else if (valid) {
         w[0] = uin[j];
@@ -487,9 +489,14 @@ __device__ __forceinline__ void tc_decode_warp(const TcCfg& tc, const float* __r
 // layers, output chunks and lobes unrolled at compile time); NL = 0: any
 // layer count and K <= KMAX. WARPDEC: the warp-per-query decode
 // (tc_decode_warp) instead of one thread per query.
-template <int KMAX, bool F2, int NL, bool WARPDEC = false>
+// Grid table type of the forward kernel: the FP16 copy, or the FP32 master
+// table (inference weights) in the FP32-accuracy mode.
+template <bool G32>
+using GridT = typename std::conditional<G32, float, __half>::type;
+
+template <int KMAX, bool F2, int NL, bool WARPDEC = false, bool G32 = false>
 __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 6) : (KMAX == 8 ? 3 : 1)) k_forward_tc(const __grid_constant__ TcCfg tc,
-                                                         const __half* __restrict__ grid_h,
+                                                         const GridT<G32>* __restrict__ grid_h,
                                                          const uint8_t* __restrict__ wblob,
                                                          const __grid_constant__ QueryBatch qb,
                                                          int* __restrict__ status) {
@@ -1342,7 +1349,8 @@ npm_status tc_create(npm_handle* h) {
         // kind::f16 descriptor: D FP32 (bit 4), A and B BF16 (bits 7, 10;
         // zero for FP16 operands), both K-major, N >> 3 at bit 17, M >> 4 at
         // bit 24.
-        const uint32_t ab = c.precision == NPM_FP16 ? 0u : (1u << 7) | (1u << 10);
+        const bool f16ops = c.precision == NPM_FP16 || c.precision == NPM_FP32_TC;
+        const uint32_t ab = f16ops ? 0u : (1u << 7) | (1u << 10);
         ly.idesc = (1u << 4) | ab | ((uint32_t)(ly.Np >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
         maxnp = ly.Np > maxnp ? ly.Np : maxnp;
     }
@@ -1360,8 +1368,9 @@ npm_status tc_create(npm_handle* h) {
     for (int l = sep0 ? 1 : 0; l < c.n_layers; ++l) maxkp1 = std::max(maxkp1, t.layer[l].Kp);
     t.a_bytes = (uint32_t)(kTile * maxkp1 * 2);
     t.a0_bytes = sep0 ? (uint32_t)(kTile * t.layer[0].Kp * 2) : 0u;
-    t.split = c.precision == NPM_BF16X3 ? 1 : 0;
-    t.f16 = c.precision == NPM_FP16 ? 1 : 0;
+    t.split = (c.precision == NPM_BF16X3 || c.precision == NPM_FP32_TC) ? 1 : 0;
+    t.f16 = (c.precision == NPM_FP16 || c.precision == NPM_FP32_TC) ? 1 : 0;
+    t.fp32 = c.precision == NPM_FP32_TC ? 1 : 0;
     const uint32_t nsplit = t.split ? 2u : 1u;
     const uint32_t nw = (t.split || t.f16) ? 2u : 1u;
     uint32_t cols = 32;
@@ -1436,7 +1445,8 @@ npm_status tc_create(npm_handle* h) {
         tr.bar_off = tr.x_off + 2 * kTile * 16;
         static_assert(2 * kTile * 16 >= 2048, "the exchange buffer covers the delta tile's over-read");
         tr.smem = tr.bar_off + 64;
-        s->can_train = fits && pw <= 512 && tr.smem <= 220 * 1024;
+        // The FP32-accuracy mode trains with the FP32 kernels.
+        s->can_train = fits && pw <= 512 && tr.smem <= 220 * 1024 && !t.fp32;
     }
     if (device_alloc((void**)&s->wblob, nw * t.w_bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -1490,10 +1500,10 @@ cudaError_t tc_refresh_weights(npm_handle* h, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int KMAX, bool F2, int NL, bool WARPDEC = false>
+template <int KMAX, bool F2, int NL, bool WARPDEC = false, bool G32 = false>
 static cudaError_t launch_tc(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStream_t st) {
     TcState* s = h->tc;
-    auto kern = k_forward_tc<KMAX, F2, NL, WARPDEC>;
+    auto kern = k_forward_tc<KMAX, F2, NL, WARPDEC, G32>;
     // CTAs per SM from registers (the instance's count, queried once) and
     // tensor memory; then carve out just the shared memory they need so the
     // rest stays L1 for the grid gathers.
@@ -1533,7 +1543,10 @@ static cudaError_t launch_tc(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaS
     if (g > hint) g = hint < 1 ? 1 : hint;
     int* status = reinterpret_cast<int*>(h->scalars + 8);
     const uint8_t* wb = h->ema ? s->wblob_inf : s->wblob;  // inference weights
-    kern<<<(int)g, kThreads, s->smem, st>>>(s->cfg, h->grid_h, wb, qb, status);
+    const GridT<G32>* grid;
+    if constexpr (G32) grid = h->ema ? h->ema : h->params;  // the inference parameters
+    else grid = h->grid_h;
+    kern<<<(int)g, kThreads, s->smem, st>>>(s->cfg, grid, wb, qb, status);
     return cudaGetLastError();
 }
 
@@ -1601,6 +1614,15 @@ cudaError_t tc_train(npm_handle* h, int64_t n, int64_t ld, const float* pos, con
 cudaError_t tc_query_batch(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStream_t st, bool pdl) {
     const int K = h->cfg.K, L = h->cfg.n_layers;
     const bool f2 = h->cfg.feat_per_level == 2;
+    // The FP32-accuracy mode gathers from the FP32 table.
+    if (h->tc->cfg.fp32) {
+        if (K <= 4) return f2 ? launch_tc<4, true, 0, false, true>(h, qb, max_n, st)
+                              : launch_tc<4, false, 0, false, true>(h, qb, max_n, st);
+        if (K <= 8) return f2 ? launch_tc<8, true, 0, false, true>(h, qb, max_n, st)
+                              : launch_tc<8, false, 0, false, true>(h, qb, max_n, st);
+        return f2 ? launch_tc<16, true, 0, false, true>(h, qb, max_n, st)
+                  : launch_tc<16, false, 0, false, true>(h, qb, max_n, st);
+    }
     // The small serving networks get their own kernel (npm_tc_tiny.cu);
     // tuning override NPM_TC_TINY=0 selects the general kernel instead.
     static std::atomic<int> env_tiny{INT32_MIN + 1};

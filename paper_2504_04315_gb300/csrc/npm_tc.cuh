@@ -34,7 +34,10 @@ struct TcCfg {
                        // 0 when layer 0 shares the buffer of layers >= 1
     int split;         // 1: BF16 residual operands (three MMAs per K step)
     int f16;           // 1: FP16 operands: activations rounded to FP16, weights
-                       // FP16 plus an FP16 residual (two MMAs per K step)
+                       // FP16 plus an FP16 residual (two MMAs per K step);
+                       // with split, activations FP16 plus an FP16 residual too
+    int fp32;          // 1: the FP32-accuracy mode (split FP16 operands, FP32
+                       // grid table, the FP32 path's sampler)
     uint32_t tmem_cols;
     int enc_width;     // meaningful network inputs
 };
@@ -145,6 +148,13 @@ __device__ __forceinline__ uint32_t pack_f16_sat(float a, float b) {
     return d;
 }
 
+// FP16 residuals (a - hi_a, b - hi_b) of a packed FP16 pair hp = (hi_a,
+// hi_b), rounded to nearest and packed the same way.
+__device__ __forceinline__ uint32_t f16_residual(uint32_t hp, float a, float b) {
+    const float2 hf = __half22float2(*reinterpret_cast<const __half2*>(&hp));
+    return pack_f16_sat(a - hf.x, b - hf.y);
+}
+
 // A pair of MMA operands in the model's operand format.
 __device__ __forceinline__ uint32_t pack_op(float a, float b, bool f16) {
     return f16 ? pack_f16_sat(a, b) : pack_bf16(a, b);
@@ -189,6 +199,14 @@ __device__ __forceinline__ void store16_fwd(uint8_t* sA, uint32_t off0, uint32_t
     if (f16) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) h[i] = pack_f16_sat(v[2 * i], v[2 * i + 1]);
+        if (lo_off) {
+            // FP16 residuals v - hi, rounded to nearest.
+            uint32_t l[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) l[i] = f16_residual(h[i], v[2 * i], v[2 * i + 1]);
+            *reinterpret_cast<uint4*>(sA + lo_off + off0) = make_uint4(l[0], l[1], l[2], l[3]);
+            *reinterpret_cast<uint4*>(sA + lo_off + off1) = make_uint4(l[4], l[5], l[6], l[7]);
+        }
     } else if (lo_off) {
         uint32_t l[8];
 #pragma unroll
@@ -215,7 +233,9 @@ __device__ __forceinline__ void store16_fwd(uint8_t* sA, uint32_t off0, uint32_t
 __device__ __forceinline__ void store_pair(uint8_t* sA, uint32_t off, float a, float b, uint32_t lo_off,
                                            bool f16 = false) {
     if (f16) {
-        *reinterpret_cast<uint32_t*>(sA + off) = pack_f16_sat(a, b);
+        const uint32_t hp = pack_f16_sat(a, b);
+        *reinterpret_cast<uint32_t*>(sA + off) = hp;
+        if (lo_off) *reinterpret_cast<uint32_t*>(sA + lo_off + off) = f16_residual(hp, a, b);
         return;
     }
     __nv_bfloat162 hb = __floats2bfloat162_rn(a, b);
@@ -228,7 +248,9 @@ __device__ __forceinline__ void store_pair(uint8_t* sA, uint32_t off, float a, f
 
 __device__ __forceinline__ void store_one(uint8_t* sA, uint32_t off, float a, uint32_t lo_off, bool f16 = false) {
     if (f16) {
-        *reinterpret_cast<uint16_t*>(sA + off) = (uint16_t)(pack_f16_sat(a, 0.0f) & 0xffffu);
+        const uint32_t hp = pack_f16_sat(a, 0.0f);
+        *reinterpret_cast<uint16_t*>(sA + off) = (uint16_t)(hp & 0xffffu);
+        if (lo_off) *reinterpret_cast<uint16_t*>(sA + lo_off + off) = (uint16_t)(f16_residual(hp, a, 0.0f) & 0xffffu);
         return;
     }
     const __nv_bfloat16 hb = __float2bfloat16_rn(a);

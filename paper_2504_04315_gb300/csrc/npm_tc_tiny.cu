@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(kThreads * kGroups, 1) k_forward_tiny(const __
 bool tiny_qualifies(const TcCfg& c) {
     const DevCfg& d = c.base;
     const uint32_t grid_bytes = (uint32_t)d.level_res[0] * d.level_res[0] * d.level_res[0] * 8u;
-    return d.mode == NPM_RADIANCE && d.n_levels == 1 && d.feat == 4 && (d.dense_mask & 1u) && d.n_layers == 3 &&
+    return !c.fp32 && d.mode == NPM_RADIANCE && d.n_levels == 1 && d.feat == 4 && (d.dense_mask & 1u) && d.n_layers == 3 &&
            d.K == 4 && d.kappa_act == NPM_SOFTPLUS && c.layer[0].Kp == 16 && c.layer[0].Np <= 32 &&
            c.layer[1].Kp == 32 && c.layer[1].Np <= 32 && c.layer[2].Kp == 32 && c.layer[2].Np == 16 &&
            c.a0_bytes == 0 && c.a_bytes == (uint32_t)(kTile * 32 * 2) && grid_bytes % 16u == 0 &&

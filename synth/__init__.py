@@ -83,7 +83,7 @@ RES16 = [16, 20, 25, 32, 40, 50, 64, 80, 101, 128, 161, 203, 256, 322, 406, 512]
 
 RADIANCE, PRODUCT = 0, 1
 SOFTPLUS, EXP = 0, 1
-FP32, BF16, BF16X3, FP16 = 0, 1, 2, 3
+FP32, BF16, BF16X3, FP16, FP32_TC = 0, 1, 2, 3, 4
 
 
 @dataclass
@@ -159,6 +159,9 @@ WORKLOADS = {
         name="tiny dense 16^3x4, MLP 4-32-32-16, K=4, split-bf16, training batch 2^18", n_train=1 << 18),
     "product_bf16": PRODUCT_BF16,
     "paper_own": PAPER_OWN,
+    "paper_hash_fp32tc": PAPER_HASH.with_(
+        name="hash grid 16 levels x 2 feats, T=2^19, MLP 32-64-64-64-32, K=8, FP32 accuracy on tensor cores "
+             "(split FP16 operands, FP32 grid)", precision=FP32_TC),
     "paper_hash_bf16": PAPER_HASH.with_(
         name="hash grid 16 levels x 2 feats, T=2^19, MLP 32-64-64-64-32, K=8, split-bf16",
         precision=BF16X3),

@@ -24,7 +24,7 @@ def _batch(w, n, seed):
     return [cuda(a) if a is not None else None for a in (b.pos, b.dir, b.radiance, b.pdf, b.aux)]
 
 
-@pytest.mark.parametrize("precision", [synth.FP32, synth.BF16X3])
+@pytest.mark.parametrize("precision", [synth.FP32, synth.BF16X3, synth.FP32_TC])
 def test_ema_tracks_oracle_and_serves_inference(precision):
     w = synth.TINY.with_(precision=precision)
     n, decay, steps = 4096, 0.9, 8

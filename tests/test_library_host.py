@@ -52,7 +52,7 @@ def test_config_struct_layout_matches_header():
 
 @pytest.mark.parametrize("field,value", [
     ("mode", 7), ("n_levels", 0), ("feat_per_level", 9), ("K", 0), ("kappa_act", 5),
-    ("precision", 4), ("log2_table", 30), ("max_batch", -1)])
+    ("precision", 5), ("log2_table", 30), ("max_batch", -1)])
 def test_invalid_config_rejected_on_host(lib, field, value):
     cfg = npm.make_config(npm.RADIANCE, [16], 4, 19, [4, 32, 32, 16], 4)
     setattr(cfg, field, value)
