@@ -494,8 +494,15 @@ __device__ __forceinline__ void tc_decode_warp(const TcCfg& tc, const float* __r
 template <bool G32>
 using GridT = typename std::conditional<G32, float, __half>::type;
 
-template <int KMAX, bool F2, int NL, bool WARPDEC = false, bool G32 = false>
-__global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 6) : (KMAX == 8 ? 3 : 1)) k_forward_tc(const __grid_constant__ TcCfg tc,
+// CTAs of G tile groups (128 threads each) share one copy of the weights;
+// each group has its own activation tiles, tensor-memory columns, MMA
+// barrier and named barrier, and walks its own tiles.
+__host__ __device__ constexpr int tc_min_blocks(int kmax, bool f2, int nl, int g) {
+    return g > 1 ? 1 : (kmax == 4 && !f2) ? (nl == 3 ? 8 : 6) : (kmax == 8 ? 3 : 1);
+}
+
+template <int KMAX, bool F2, int NL, bool WARPDEC = false, bool G32 = false, int G = 1>
+__global__ void __launch_bounds__(kThreads * G, tc_min_blocks(KMAX, F2, NL, G)) k_forward_tc(const __grid_constant__ TcCfg tc,
                                                          const GridT<G32>* __restrict__ grid_h,
                                                          const uint8_t* __restrict__ wblob,
                                                          const __grid_constant__ QueryBatch qb,
@@ -503,37 +510,43 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 
     extern __shared__ __align__(1024) uint8_t smem[];
     const int nsplit = tc.split ? 2 : 1;               // activation tiles (hi, residual)
     const int nw = (tc.split || tc.f16) ? 2 : 1;       // weight blobs (hi, residual)
+    const int g = G > 1 ? (int)(threadIdx.x >> 7) : 0;  // tile group
+    const int t = G > 1 ? (int)(threadIdx.x & 127) : (int)threadIdx.x;  // row of the group's tile
+    const int warp = t >> 5;                            // warp of the group (its TMEM lane quarter)
+    const uint32_t gbytes = nsplit * (tc.a0_bytes + tc.a_bytes);  // activation tiles of a group
     uint8_t* sW = smem;
-    uint8_t* sA = smem + nw * tc.w_bytes + nsplit * tc.a0_bytes;  // inputs of layers >= 1
-    uint8_t* sA0 = tc.a0_bytes ? smem + nw * tc.w_bytes : sA;     // layer-0 input (encoding)
+    uint8_t* sG0 = smem + nw * tc.w_bytes;
+    uint8_t* sA = sG0 + g * gbytes + nsplit * tc.a0_bytes;  // inputs of layers >= 1
+    uint8_t* sA0 = tc.a0_bytes ? sG0 + g * gbytes : sA;    // layer-0 input (encoding)
     const uint32_t a0_lo = tc.a0_bytes ? tc.a0_bytes : tc.a_bytes;  // its residual tile
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sA + nsplit * tc.a_bytes);  // [0] mma, [1] weights
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
-    const int t = threadIdx.x;
-    const int warp = t >> 5;
-    const uint32_t bar_mma = smem_u32(&bars[0]);
-    const uint32_t bar_w = smem_u32(&bars[1]);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sG0 + G * gbytes);  // [0] weights, [1 + g] mma
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 1 + G);
+    const uint32_t bar_mma = smem_u32(&bars[1 + g]);
+    const uint32_t bar_w = smem_u32(&bars[0]);
+    // Tensor-memory columns of the CTA (a power of two: the groups' columns
+    // rounded up).
+    uint32_t cta_cols = 32;
+    while (cta_cols < (uint32_t)G * tc.tmem_cols) cta_cols <<= 1;
 
-    if (warp == 0) {
+    if (threadIdx.x < 32) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tslot)),
-                     "r"(tc.tmem_cols)
+                     "r"(cta_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (t == 0) {
-        mbar_init(bar_mma, 1);
-        mbar_init(bar_w, 1);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i <= G; ++i) mbar_init(smem_u32(&bars[i]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *tslot;
+    const uint32_t tmem = *tslot + (uint32_t)g * tc.tmem_cols;
 
     // Weights: one bulk asynchronous copy global -> shared.
-    if (t == 0) {
+    if (threadIdx.x == 0) {
         const uint32_t wb = (uint32_t)nw * tc.w_bytes;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_w), "r"(wb)
                      : "memory");
@@ -553,7 +566,7 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 
                 *reinterpret_cast<uint4*>(sA0 + a0_lo + tile_off(t, 8 * c, kp0)) = make_uint4(0u, 0u, 0u, 0u);
         }
     }
-    bool ok = !__syncthreads_or(warp == 0 && !mbar_wait_bounded(bar_w, 0));
+    bool ok = !__syncthreads_or(threadIdx.x < 32 && !mbar_wait_bounded(bar_w, 0));
     uint32_t phase = 0;
     const uint32_t sA_addr = smem_u32(sA), sA0_addr = smem_u32(sA0);
     const uint32_t sW_addr = smem_u32(sW);
@@ -567,7 +580,8 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 
         n0 = *qb.n_dev;
         ntiles = (n0 + kTile - 1) / kTile;
     }
-    for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * G;
+    for (int64_t tile = (int64_t)blockIdx.x * G + g; ok && tile < ntiles; tile += stride) {
         int sg = 0;
         while (sg + 1 < qb.nseg && tile >= qb.seg[sg + 1].tile0) ++sg;
         const QuerySeg& S = qb.seg[sg];
@@ -587,7 +601,7 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 
                 if ((r < 3 || S.ufrac > 0.0f) && b0 < n)
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(S.uin + r * ld + b0));
             } else if (r < 7) {
-                const int64_t nt = tile + gridDim.x;
+                const int64_t nt = tile + stride;
                 if (nt < ntiles) {
                     int s2 = sg;
                     while (s2 + 1 < qb.nseg && nt >= qb.seg[s2 + 1].tile0) ++s2;
@@ -604,7 +618,7 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 
                       tc.base.n_levels, true);
         fence_async_smem();
         tc_fence_before();
-        __syncthreads();
+        tc_group_sync(g);
         uint32_t raw[4 * KMAX / 16][16];
 #pragma unroll kUnrollL
         for (int l = 0; l < L; ++l) {
@@ -632,11 +646,11 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 
                 mma_commit(bar_mma);
             }
             // Warp 0 (which holds the issuing thread) waits on the MMA's
-            // barrier; the other warps wait in the CTA barrier, issuing
+            // barrier; the other warps wait in the group barrier, issuing
             // nothing, and see the accumulators after its fence.
             const bool done = warp != 0 || mbar_wait_bounded(bar_mma, phase);
             phase ^= 1u;
-            ok = !__syncthreads_or(!done);
+            ok = !tc_group_sync_or(g, !done);
             if (!ok) break;
             tc_fence_after();
             if (l < L - 1) {
@@ -654,7 +668,7 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 
                 }
                 fence_async_smem();
                 tc_fence_before();
-                __syncthreads();
+                tc_group_sync(g);
             } else {
 #pragma unroll
                 for (int c = 0; c < 4 * KMAX / 16; ++c)
@@ -678,10 +692,10 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 
                     for (int q = 0; q < 4; ++q)
                         *reinterpret_cast<uint4*>(sRaw + t * RS + 16 * c + 4 * q) =
                             make_uint4(raw[c][4 * q], raw[c][4 * q + 1], raw[c][4 * q + 2], raw[c][4 * q + 3]);
-            __syncthreads();
+            tc_group_sync(g);
             tc_decode_warp<KMAX>(tc, sRaw, warp, t & 31, (tile - S.tile0) * kTile, n, ld, S.uin, S.ufrac,
                                  qb.sample != 0, S.dir, S.pdf, S.mix, qb.log_pdf != 0);
-            __syncthreads();
+            tc_group_sync(g);
         } else {
             float rawf[4 * KMAX];
 #pragma unroll
@@ -695,7 +709,7 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 
     if (!ok) {
         if (t == 0) atomicOr(status, kStatusTimeout);
         // Before the tensor memory is released: wait again, bounded, for this
-        // CTA's own asynchronous work that may still be in flight (the
+        // group's own asynchronous work that may still be in flight (the
         // weights' bulk copy; the MMA batch whose wait gave up, the phase
         // before `phase`).
         if (warp == 0) {
@@ -705,10 +719,9 @@ __global__ void __launch_bounds__(kThreads, (KMAX == 4 && !F2) ? (NL == 3 ? 8 : 
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (threadIdx.x < 32) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(tc.tmem_cols)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(cta_cols)
                      : "memory");
     }
 }
@@ -1500,10 +1513,25 @@ cudaError_t tc_refresh_weights(npm_handle* h, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int KMAX, bool F2, int NL, bool WARPDEC = false, bool G32 = false>
+// Shared memory of a k_forward_tc CTA of G tile groups: the weight blobs,
+// each group's activation tiles, the barriers and the tensor-memory slot.
+static size_t tc_group_smem(const TcState* s, int G) {
+    const TcCfg& c = s->cfg;
+    const size_t nw = (c.split || c.f16) ? 2 : 1, nsplit = c.split ? 2 : 1;
+    return nw * c.w_bytes + (size_t)G * nsplit * (c.a0_bytes + c.a_bytes) + 8 * (1 + G) + 16;
+}
+
+// Whether a CTA of G tile groups fits one SM (shared and tensor memory).
+static bool tc_groups_fit(const TcState* s, int G) {
+    uint32_t cols = 32;
+    while (cols < (uint32_t)G * s->cfg.tmem_cols) cols <<= 1;
+    return cols <= 512u && tc_group_smem(s, G) + 1024 <= 227 * 1024;
+}
+
+template <int KMAX, bool F2, int NL, bool WARPDEC = false, bool G32 = false, int G = 1>
 static cudaError_t launch_tc(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStream_t st) {
     TcState* s = h->tc;
-    auto kern = k_forward_tc<KMAX, F2, NL, WARPDEC, G32>;
+    auto kern = k_forward_tc<KMAX, F2, NL, WARPDEC, G32, G>;
     // CTAs per SM from registers (the instance's count, queried once) and
     // tensor memory; then carve out just the shared memory they need so the
     // rest stays L1 for the grid gathers.
@@ -1526,8 +1554,10 @@ static cudaError_t launch_tc(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaS
     const int v = env_override("NPM_TC_CTAS_PER_SM", env_ctas);
     if (v >= 1 && v < per_sm) per_sm = v;
     if (per_sm < 1) per_sm = 1;
+    const size_t smem = G > 1 ? tc_group_smem(s, G) : s->smem;
+    if (G > 1) per_sm = 1;  // one CTA of G groups per SM
     static std::atomic<uint64_t> attrs{~0ull};
-    cudaError_t e = set_smem_attrs(kern, s->smem, carveout_percent((size_t)per_sm * (s->smem + 1024)), attrs);
+    cudaError_t e = set_smem_attrs(kern, smem, carveout_percent((size_t)per_sm * (smem + 1024)), attrs);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -1538,7 +1568,7 @@ static cudaError_t launch_tc(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaS
         t0 += (qb.seg[i].n + kTile - 1) / kTile;
     }
     qb.total_tiles = t0;
-    const int64_t hint = qb.n_dev ? (max_n + kTile - 1) / kTile : t0;
+    const int64_t hint = (qb.n_dev ? (max_n + kTile - 1) / kTile : t0 + G - 1) / G;
     int64_t g = (int64_t)per_sm * sms;
     if (g > hint) g = hint < 1 ? 1 : hint;
     int* status = reinterpret_cast<int*>(h->scalars + 8);
@@ -1546,7 +1576,7 @@ static cudaError_t launch_tc(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaS
     const GridT<G32>* grid;
     if constexpr (G32) grid = h->ema ? h->ema : h->params;  // the inference parameters
     else grid = h->grid_h;
-    kern<<<(int)g, kThreads, s->smem, st>>>(s->cfg, grid, wb, qb, status);
+    kern<<<(int)g, kThreads * G, smem, st>>>(s->cfg, grid, wb, qb, status);
     return cudaGetLastError();
 }
 
@@ -1615,11 +1645,24 @@ cudaError_t tc_query_batch(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStr
     const int K = h->cfg.K, L = h->cfg.n_layers;
     const bool f2 = h->cfg.feat_per_level == 2;
     // The FP32-accuracy mode gathers from the FP32 table.
+    // Up to eight lobes it runs three tile groups per CTA sharing one copy
+    // of the weights where they fit (more tiles in flight per SM for the
+    // gathers' latency than separate CTAs, whose weight copies fill the
+    // shared memory).
     if (h->tc->cfg.fp32) {
-        if (K <= 4) return f2 ? launch_tc<4, true, 0, false, true>(h, qb, max_n, st)
-                              : launch_tc<4, false, 0, false, true>(h, qb, max_n, st);
-        if (K <= 8) return f2 ? launch_tc<8, true, 0, false, true>(h, qb, max_n, st)
-                              : launch_tc<8, false, 0, false, true>(h, qb, max_n, st);
+        const bool grp = tc_groups_fit(h->tc, 3);
+        if (K <= 4) {
+            if (grp) return f2 ? launch_tc<4, true, 0, false, true, 3>(h, qb, max_n, st)
+                               : launch_tc<4, false, 0, false, true, 3>(h, qb, max_n, st);
+            return f2 ? launch_tc<4, true, 0, false, true>(h, qb, max_n, st)
+                      : launch_tc<4, false, 0, false, true>(h, qb, max_n, st);
+        }
+        if (K <= 8) {
+            if (grp) return f2 ? launch_tc<8, true, 0, false, true, 3>(h, qb, max_n, st)
+                               : launch_tc<8, false, 0, false, true, 3>(h, qb, max_n, st);
+            return f2 ? launch_tc<8, true, 0, false, true>(h, qb, max_n, st)
+                      : launch_tc<8, false, 0, false, true>(h, qb, max_n, st);
+        }
         return f2 ? launch_tc<16, true, 0, false, true>(h, qb, max_n, st)
                   : launch_tc<16, false, 0, false, true>(h, qb, max_n, st);
     }

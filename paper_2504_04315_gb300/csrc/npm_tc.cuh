@@ -148,6 +148,25 @@ __device__ __forceinline__ uint32_t pack_f16_sat(float a, float b) {
     return d;
 }
 
+// Named barrier of 128-thread tile group g of a CTA (id 1 + g; id 0 is the
+// CTA-wide __syncthreads), and its form that also ORs a predicate over the
+// group's threads.
+__device__ __forceinline__ void tc_group_sync(int g) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(128) : "memory");
+}
+__device__ __forceinline__ bool tc_group_sync_or(int g, bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred q, o;\n\t"
+        "setp.ne.u32 q, %3, 0;\n\t"
+        "bar.red.or.pred o, %1, %2, q;\n\t"
+        "selp.u32 %0, 1, 0, o;\n\t}\n"
+        : "=r"(r)
+        : "r"(1 + g), "r"(128), "r"((uint32_t)p)
+        : "memory");
+    return r != 0;
+}
+
 // FP16 residuals (a - hi_a, b - hi_b) of a packed FP16 pair hp = (hi_a,
 // hi_b), rounded to nearest and packed the same way.
 __device__ __forceinline__ uint32_t f16_residual(uint32_t hp, float a, float b) {
