@@ -181,6 +181,33 @@ def scatter_atomic_counts(model, w, pos_dev):
     return n4, n2
 
 
+def gather_sector_counts(model, w, pos_dev):
+    """32-byte L2 sectors that a batch's grid gathers must touch: per query
+    and level, the distinct sectors holding the 8 corners' FP32 entries
+    (feat x 4 bytes each, at the level's table offset), counted from the
+    corner indices the library forms (npm_grid_indices)."""
+    import torch
+    idx = model.grid_indices(pos_dev).to(torch.int64)  # [L][8][n], entry within the level
+    offs = torch.tensor(np.cumsum([0] + synth.grid_sizes(w)[:-1]), dtype=torch.int64,
+                        device=idx.device)[:, None, None]
+    fb = 4 * w.feat
+    first = ((offs + idx) * fb) // 32                   # sector of each entry's first byte
+    last = ((offs + idx) * fb + fb - 1) // 32           # and of its last byte
+    sec = torch.cat([first, last], 1).sort(1).values    # [L][16][n]
+    distinct = 1 + (sec[:, 1:, :] != sec[:, :-1, :]).sum(1)
+    return int(distinct.sum())
+
+
+def gather_roofline(qps, sectors_per_query, up):
+    """Forward bound of the FP32-accuracy tensor-core mode: its grid gathers
+    at the measured random 32-byte L2 sector rate (the MLP's tensor work and
+    the table, resident in L2, are far below their own limits)."""
+    peak = up["l2_sector_read_gbs"] * 1e9 / (32.0 * sectors_per_query)
+    return {"bound": "l2", "achieved": qps, "peak": peak, "unit": "queries/s", "frac": qps / peak,
+            "sectors_per_query": sectors_per_query,
+            "peak_source": "random 32-byte L2 sector reads, measured (unit_peaks.l2_sector_read_gbs)"}
+
+
 def train_roofline(sps, w, n_params, pk, up, atomics=None):
     """Training step bound: dense Adam over every parameter (HBM, 34 B each)
     plus the grid scatter at the measured L2 atomic rates; the forward
@@ -409,6 +436,34 @@ def main():
         d2h = n * 4 * 4
         e2e = {"value": n * ke * world / e2e_s, "unit": "queries/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # The same workload and inputs in the FP32-accuracy tensor-core mode
+    # (held to the FP32 path's bars), when the headline runs in FP32.
+    fp32_tc = None
+    if not args.no_extras and not train_mode and w.precision == synth.FP32:
+        mt = npm.NPM(npm.config_from(w, max_batch=n, precision=synth.FP32_TC))
+        mt.set_params(params)
+        for i in range(3):
+            mt.query_sample(pos[i], uu[i], aux[i], out=outs[i], stream=stream)
+        kt = max(5, K // 2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(kt):
+            k = i % nrot
+            mt.query_sample(pos[k], uu[k], aux[k], out=outs[k], stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tc_ms = e0.elapsed_time(e1) / kt
+        fp32_tc = {"value": n * world / (tc_ms / 1e3), "unit": "queries/s", "ms_per_step": tc_ms,
+                   "over_fp32_cuda_cores": (n / (tc_ms / 1e3)) / (n / (kern_ms / 1e3)),
+                   "sectors_per_query": gather_sector_counts(mt, w, pos[0][:, :1 << 16].contiguous()) / (1 << 16),
+                   "mode": "NPM_FP32_TC: FP32 grid table; activations and weights as FP16 high part plus "
+                           "FP16 residual, three tcgen05 MMAs per K step, FP32 accumulation; the FP32 "
+                           "path's decode and sampler. Held to the FP32 bars (density and direction "
+                           "within 1e-4 of the FP64 oracle)",
+                   "kernel": "k_forward_tc<8, 1, 0, 0, 1, 3> (three tile groups per SM)"}
+        mt.close()
 
     # Reduced-precision serving path: the tiny model at 2^22 queries per
     # call in split BF16 on tensor cores, next to the FP32 CUDA-core path on
@@ -643,6 +698,7 @@ def main():
                      if (w.precision == synth.FP32 and not train_mode) else None),
         "clocks": clocks,
         "train": train,
+        "fp32_tensor_cores": fp32_tc,
         "reduced_precision": reduced,
         "serving": serving,
         "server": server,
@@ -650,6 +706,9 @@ def main():
         "unit_peaks": unit_peaks,
     }
     if unit_peaks:
+        if fp32_tc:
+            fp32_tc["roofline"] = gather_roofline(fp32_tc["value"] / world, fp32_tc["sectors_per_query"],
+                                                  unit_peaks)
         if reduced:
             reduced["roofline"] = tc_roofline(reduced["split_bf16"], synth.TINY_BF16, pk, unit_peaks,
                                               props.multi_processor_count, sm_max)

@@ -3,6 +3,7 @@ it divides by, and the bound it picks, against hand-computed values."""
 import os
 import sys
 
+import numpy as np
 import pytest
 
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
@@ -58,3 +59,39 @@ def test_serving_roofline_sums_queries_compaction_and_training():
     c_s = 8 * 6_500_000 / 8000e9
     assert r["bound_ms_per_frame"] == pytest.approx((q_s + c_s + 20e-6) * 1e3)
     assert r["frac"] == pytest.approx((q_s + c_s + 20e-6) / 0.7e-3)
+
+
+class _FakeIdx:
+    """Stands in for a model: grid_indices returns fixed corner indices."""
+
+    def __init__(self, idx):
+        self.idx = idx
+
+    def grid_indices(self, pos):
+        import torch
+        return torch.as_tensor(self.idx)
+
+
+def test_gather_sector_counts_by_hand():
+    torch = pytest.importorskip("torch")
+    w = synth.PAPER_HASH  # two FP32 features: 8-byte entries, four to a sector
+    L = len(w.level_res)
+    offs = np.cumsum([0] + synth.grid_sizes(w)[:-1])
+    idx = np.zeros((L, 8, 2), np.int64)
+    # Query 0: every level's corners are entries 0..7 (two sectors when the
+    # level starts on a sector boundary). Query 1: eight corners 64 entries
+    # apart (eight sectors).
+    idx[:, :, 0] = np.arange(8)[None, :]
+    idx[:, :, 1] = 64 * np.arange(8)[None, :]
+    expect = 0
+    for l in range(L):
+        s0 = {((offs[l] + e) * 8) // 32 for e in range(8)}
+        expect += len(s0) + 8
+    got = bench.gather_sector_counts(_FakeIdx(idx), w, torch.zeros((3, 2)))
+    assert got == expect
+
+
+def test_gather_roofline_arithmetic():
+    r = bench.gather_roofline(2e9, 96.0, {"l2_sector_read_gbs": 9600.0})
+    assert r["peak"] == pytest.approx(9600e9 / (32 * 96.0))
+    assert r["frac"] == pytest.approx(2e9 / r["peak"])
