@@ -1695,7 +1695,12 @@ cudaError_t tc_query_batch(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStr
         if (L == 3 && K == 4 && !f2) return launch_tc<4, false, 3>(h, qb, max_n, st);
         return f2 ? launch_tc<4, true, 0>(h, qb, max_n, st) : launch_tc<4, false, 0>(h, qb, max_n, st);
     }
-    if (K <= 8) return f2 ? launch_tc<8, true, 0>(h, qb, max_n, st) : launch_tc<8, false, 0>(h, qb, max_n, st);
+    if (K <= 8) {
+        // Hash-grid networks: three tile groups sharing the weights, where
+        // they fit (more tiles in flight for the gathers).
+        if (f2 && tc_groups_fit(h->tc, 3)) return launch_tc<8, true, 0, false, false, 3>(h, qb, max_n, st);
+        return f2 ? launch_tc<8, true, 0>(h, qb, max_n, st) : launch_tc<8, false, 0>(h, qb, max_n, st);
+    }
     return f2 ? launch_tc<16, true, 0>(h, qb, max_n, st) : launch_tc<16, false, 0>(h, qb, max_n, st);
 }
 
