@@ -34,12 +34,15 @@ def _need_cuda():
         pytest.skip("needs a CUDA GPU")
 
 
+@pytest.mark.parametrize("precision", [synth.FP32, synth.FP32_TC], ids=["fp32", "fp32-tc"])
 @pytest.mark.parametrize("w", SHAPES, ids=lambda w: w.name[:24])
-def test_fp32_sampling_and_indices(w):
+def test_fp32_sampling_and_indices(w, precision):
+    # Both FP32-accuracy paths (CUDA cores; tensor cores with split FP16
+    # operands) at the FP32 bars.
     n = 3000
     params = synth.random_params(w, 31)
     pos, u = synth.positions(31, n), synth.sample_uniforms(31, n)
-    m = make_model(w, params, n)
+    m = make_model(w, params, n, precision=precision)
     assert np.array_equal(host(m.grid_indices(cuda(pos))), oracle.grid_indices(w, pos))
     d, p, _ = m.query_sample(cuda(pos), cuda(u))
     stats = compare_samples(w, params, pos, u, None, 0.0, host(d), host(p), PDF_RTOL_FP32,
