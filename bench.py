@@ -302,7 +302,8 @@ def run_reference(args, w, rank):
         "config": {"workload": w.name, ("samples_per_step" if train_mode else "queries_per_step"): n,
                    "sample_of": total},
         "cpu_baseline": {"value": v, "unit": unit, "cores": cores, "kind": "oracle",
-                         "sample": f"{n} {what} per step of the {total}-{what[:-1]} workload"},
+                         "sample": f"{n} {what} per step of the {total}-{'sample' if train_mode else 'query'} "
+                                   "workload"},
         "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
