@@ -20,7 +20,7 @@ def _need_cuda():
         pytest.skip("needs a CUDA GPU")
 
 
-@pytest.mark.parametrize("precision", [synth.FP32, synth.BF16X3])
+@pytest.mark.parametrize("precision", [synth.FP32, synth.BF16X3, synth.FP16, synth.FP32_TC])
 def test_graph_replay_matches_eager(precision):
     import paper_2504_04315_gb300 as npm
     w = synth.TINY
