@@ -488,15 +488,18 @@ __device__ __forceinline__ void tc_decode_warp(const TcCfg& tc, const float* __r
 // NL > 0: the network has exactly NL layers and KMAX lobes (loops over
 // layers, output chunks and lobes unrolled at compile time); NL = 0: any
 // layer count and K <= KMAX. WARPDEC: the warp-per-query decode
-// (tc_decode_warp) instead of one thread per query.
+// (tc_decode_warp) instead of one thread per query. G32: the grid table is
+// the FP32 master table (the FP32-accuracy mode). G: tile groups per CTA.
 // Grid table type of the forward kernel: the FP16 copy, or the FP32 master
 // table (inference weights) in the FP32-accuracy mode.
 template <bool G32>
 using GridT = typename std::conditional<G32, float, __half>::type;
 
-// CTAs of G tile groups (128 threads each) share one copy of the weights;
+// A CTA of G tile groups (128 threads each) holds one copy of the weights;
 // each group has its own activation tiles, tensor-memory columns, MMA
-// barrier and named barrier, and walks its own tiles.
+// barrier and named barrier, and walks its own tiles. Such a CTA runs alone
+// on its SM; single-group CTAs are compiled for as many per SM as the
+// shapes that use them fit.
 __host__ __device__ constexpr int tc_min_blocks(int kmax, bool f2, int nl, int g) {
     return g > 1 ? 1 : (kmax == 4 && !f2) ? (nl == 3 ? 8 : 6) : (kmax == 8 ? 3 : 1);
 }
