@@ -975,9 +975,10 @@ __global__ void __launch_bounds__(256) k_train_encode(const __grid_constant__ De
 }
 
 // The small four-lobe instance (single-level grids) is compiled for three
-// CTAs per SM (it fits 80 registers without spills, and its delta tiles are
-// only as wide as its layers): its tile chain of MMA round trips is
-// latency-bound, and the other CTAs overlap it.
+// CTAs per SM (80 registers without spills; its delta tiles are only as
+// wide as its layers, 53 KB a CTA): its tile chain of MMA round trips is
+// latency-bound, and the other CTAs overlap it. (Four CTAs at 64 registers
+// measured slower.)
 __host__ __device__ constexpr int train_ctas_per_sm(int kmax, bool f2) { return (kmax == 4 && !f2) ? 3 : 1; }
 
 template <int KMAX, bool F2>
@@ -1430,12 +1431,6 @@ npm_status tc_create(npm_handle* h) {
         tr.split = 1;
         int maxkp = 0;
         for (int l = 0; l < c.n_layers; ++l) maxkp = std::max(maxkp, t.layer[l].Kp);
-        tr.hlo_off = off;  // one residual activation tile, reused layer by layer
-        if (tr.split) off += (uint32_t)(kTile * maxkp * 2);
-        // The encoder writes its residual at (tile + a_bytes): point that at
-        // the shared residual tile.
-        s->train_cfg.split = tr.split;
-        s->train_cfg.a_bytes = tr.split ? tr.hlo_off - tr.h_off[0] : 0u;
         col0 = (col0 + 15) / 16 * 16;
         cols = col0;
         for (int l = 0; l < c.n_layers; ++l) {
@@ -1449,18 +1444,29 @@ npm_status tc_create(npm_handle* h) {
         // weight-gradient MMA reads it transposed with M = 128 output rows:
         // rows beyond the layer's outputs come from the next row groups and,
         // past the last one, up to 2 KB beyond the tile (the residual tile
-        // and the exchange buffer that follow); they land in weight-gradient
-        // rows that are never read.
+        // that follows); they land in weight-gradient rows that are never
+        // read.
         uint32_t dcols = 16;
         for (int l = 0; l < c.n_layers; ++l)
             dcols = std::max<uint32_t>(dcols, (uint32_t)std::max(t.layer[l].Kp, t.layer[l].Np));
         tr.d_cols = dcols;
         tr.d_off = (off + 127u) / 128u * 128u;
         tr.dlo_off = tr.d_off + kTile * dcols * 2;
-        tr.x_off = tr.dlo_off + (tr.split ? kTile * dcols * 2 : 0);
-        tr.bar_off = tr.x_off + 2 * kTile * 16;
-        static_assert(2 * kTile * 16 >= 2048, "the exchange buffer covers the delta tile's over-read");
+        // One residual activation tile, reused layer by layer; the loss
+        // step's exchange of partial log-sum-exps reuses it too (the forward
+        // has finished with it, and the next tile's encode rewrites it after
+        // the backward).
+        tr.hlo_off = tr.dlo_off + kTile * dcols * 2;
+        const uint32_t hlo_bytes = (uint32_t)(kTile * maxkp * 2);
+        // (Kp >= 16, so the tile has at least 4 KB: the exchange buffer's
+        // 2 x kTile float4 and the over-read's 2 KB.)
+        tr.x_off = tr.hlo_off;
+        tr.bar_off = tr.hlo_off + hlo_bytes;
         tr.smem = tr.bar_off + 64;
+        // The encoder writes its residual at (tile + a_bytes): point that at
+        // the shared residual tile.
+        s->train_cfg.split = tr.split;
+        s->train_cfg.a_bytes = tr.hlo_off - tr.h_off[0];
         // The FP32-accuracy mode trains with the FP32 kernels.
         s->can_train = fits && pw <= 512 && tr.smem <= 220 * 1024 && !t.fp32;
     }
