@@ -1537,9 +1537,16 @@ static bool tc_groups_fit(const TcState* s, int G) {
     return cols <= 512u && tc_group_smem(s, G) + 1024 <= 227 * 1024;
 }
 
+// Whether a group's activation tiles hold the raw outputs of a 128-row tile
+// staged for the warp-per-query decode (row stride 4 KMAX + 4 floats).
+static bool tc_stage_fits(const TcState* s, int kmax) {
+    return (size_t)(s->cfg.split ? 2 : 1) * s->cfg.a_bytes >= (size_t)kTile * (4 * kmax + 4) * sizeof(float);
+}
+
 template <int KMAX, bool F2, int NL, bool WARPDEC = false, bool G32 = false, int G = 1>
 static cudaError_t launch_tc(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStream_t st) {
     TcState* s = h->tc;
+    if (WARPDEC && !tc_stage_fits(s, KMAX)) return cudaErrorInvalidValue;  // the dispatch checks this
     auto kern = k_forward_tc<KMAX, F2, NL, WARPDEC, G32, G>;
     // CTAs per SM from registers (the instance's count, queried once) and
     // tensor memory; then carve out just the shared memory they need so the
@@ -1689,7 +1696,7 @@ cudaError_t tc_query_batch(npm_handle* h, QueryBatch& qb, int64_t max_n, cudaStr
     static std::atomic<int> env_dec{INT32_MIN + 1};
     const TcCfg& c = h->tc->cfg;
     const int kmax = K <= 4 ? 4 : 8;
-    const bool fits = (size_t)(c.split ? 2 : 1) * c.a_bytes >= (size_t)kTile * (16 * kmax + 16);
+    const bool fits = tc_stage_fits(h->tc, kmax);
     if (env_override("NPM_TC_DECODE", env_dec) == 1 && K <= 8 && fits) {
         if (K <= 4) {
             if (L == 3 && K == 4 && !f2) return launch_tc<4, false, 3, true>(h, qb, max_n, st);
