@@ -1114,14 +1114,19 @@ __global__ void __launch_bounds__(kTrainThreads, train_ctas_per_sm(KMAX, F2)) k_
             const TcLayer& ly = tc.layer[l];
             if (t == 0) {
                 tc_fence_after();
+                // The descriptors of K step s are those of step 0 with the
+                // start address 256 bytes (16 units) further.
                 const uint32_t sbo = (uint32_t)(ly.Kp >> 3) * 128u;
+                const uint64_t ad0 = umma_desc(base_addr + tt.h_off[l], 128u, sbo);
+                const uint64_t bd0 = umma_desc(sW_addr + ly.w_off, 128u, sbo);
+                const uint64_t bl0 = umma_desc(sW_addr + wlo + ly.w_off, 128u, sbo);
+                const uint64_t al0 = umma_desc(hlo_addr, 128u, sbo);
                 for (int s = 0; s < (ly.Kp >> 4); ++s) {
-                    const uint64_t ad = umma_desc(base_addr + tt.h_off[l] + s * 256u, 128u, sbo);
-                    const uint64_t bd = umma_desc(sW_addr + ly.w_off + s * 256u, 128u, sbo);
-                    mma_bf16(tmem, ad, bd, ly.idesc, s > 0 ? 1u : 0u);
+                    const uint64_t o = (uint64_t)(16 * s);
+                    mma_bf16(tmem, ad0 + o, bd0 + o, ly.idesc, s > 0 ? 1u : 0u);
                     if (tt.split) {
-                        mma_bf16(tmem, ad, umma_desc(sW_addr + wlo + ly.w_off + s * 256u, 128u, sbo), ly.idesc, 1u);
-                        mma_bf16(tmem, umma_desc(hlo_addr + s * 256u, 128u, sbo), bd, ly.idesc, 1u);
+                        mma_bf16(tmem, ad0 + o, bl0 + o, ly.idesc, 1u);
+                        mma_bf16(tmem, al0 + o, bd0 + o, ly.idesc, 1u);
                     }
                 }
                 mma_commit(bar_mma);
@@ -1193,24 +1198,27 @@ __global__ void __launch_bounds__(kTrainThreads, train_ctas_per_sm(KMAX, F2)) k_
             if (t == 0) {
                 tc_fence_after();
                 const uint32_t hk = (uint32_t)(ly.Kp >> 3) * 128u;  // K step of an H_l / W_l tile
+                // Step-0 descriptors; step s adds its byte offset >> 4 to the
+                // start address field.
                 // dW_l += D^T H_l: M = 128 (outputs), N = Kp_l, K = 128 samples.
+                const uint64_t bh0 = umma_desc(base_addr + tt.h_off[l], hk, 128u);
+                const uint64_t dw0 = umma_desc(sD_addr, drg, 128u), dwl0 = umma_desc(dlo_addr, drg, 128u);
+                const uint64_t bstep = (uint64_t)((2u * hk) >> 4), dstep = (uint64_t)((2u * drg) >> 4);
                 for (int s = 0; s < 8; ++s) {
-                    const uint64_t bh = umma_desc(base_addr + tt.h_off[l] + s * 2u * hk, hk, 128u);
-                    mma_bf16(tmem + tt.dw_col[l], umma_desc(sD_addr + s * 2u * drg, drg, 128u), bh,
-                             tt.idesc_dw[l], (first && s == 0) ? 0u : 1u);
-                    if (tt.split)
-                        mma_bf16(tmem + tt.dw_col[l], umma_desc(dlo_addr + s * 2u * drg, drg, 128u), bh,
-                                 tt.idesc_dw[l], 1u);
+                    const uint64_t bh = bh0 + s * bstep;
+                    mma_bf16(tmem + tt.dw_col[l], dw0 + s * dstep, bh, tt.idesc_dw[l], (first && s == 0) ? 0u : 1u);
+                    if (tt.split) mma_bf16(tmem + tt.dw_col[l], dwl0 + s * dstep, bh, tt.idesc_dw[l], 1u);
                 }
                 // D W_l: M = 128 samples, N = Kp_l, K = Np_l outputs.
+                const uint64_t ad0 = umma_desc(sD_addr, 128u, drg), al0 = umma_desc(dlo_addr, 128u, drg);
+                const uint64_t bd0 = umma_desc(sW_addr + ly.w_off, hk, 128u);
+                const uint64_t bl0 = umma_desc(sW_addr + wlo + ly.w_off, hk, 128u);
                 for (int s = 0; s < (ly.Np >> 4); ++s) {
-                    const uint64_t ad = umma_desc(sD_addr + s * 256u, 128u, drg);
-                    const uint64_t bd = umma_desc(sW_addr + ly.w_off + s * 2u * hk, hk, 128u);
-                    mma_bf16(tmem, ad, bd, tt.idesc_dx[l], s > 0 ? 1u : 0u);
+                    const uint64_t o = (uint64_t)(16 * s), ob = s * bstep;
+                    mma_bf16(tmem, ad0 + o, bd0 + ob, tt.idesc_dx[l], s > 0 ? 1u : 0u);
                     if (tt.split) {
-                        mma_bf16(tmem, ad, umma_desc(sW_addr + wlo + ly.w_off + s * 2u * hk, hk, 128u),
-                                 tt.idesc_dx[l], 1u);
-                        mma_bf16(tmem, umma_desc(dlo_addr + s * 256u, 128u, drg), bd, tt.idesc_dx[l], 1u);
+                        mma_bf16(tmem, ad0 + o, bl0 + ob, tt.idesc_dx[l], 1u);
+                        mma_bf16(tmem, al0 + o, bd0 + ob, tt.idesc_dx[l], 1u);
                     }
                 }
                 mma_commit(bar_mma);
